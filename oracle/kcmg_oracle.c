@@ -1,0 +1,625 @@
+/*
+ * kcmg_oracle.c -- plain, slow, obviously-correct FP64 CPU reference of the K-cycle
+ * orthonormalization multigrid (OrthoMG) solve of Toprak & Kummer, "A Task Parallel
+ * Orthonormalization Multigrid Method for Multiphase Elliptic Problems".
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may link, load or call this
+ * file; it is used by the tests, by the smoke check and by the benchmark's CPU-baseline
+ * leg.  It shares no code, header, table or helper with the CUDA library.
+ *
+ * What it follows:
+ *   rm_step     Alg. 1 (residual minimization): w = A z; modified Gram-Schmidt of w against
+ *               the stored orthonormal W with the same coefficients applied to z against Z;
+ *               normalise; append; alpha_{l+1} = w_{l+1} . r0; x = x0 + Z alpha;
+ *               r = r0 - W alpha.
+ *   mg          Alg. 2 (orthonormalization multigrid, multiplicative K-cycle): while
+ *               ||r|| > eps: pre-smoother, RM, restrict, recursive MG or direct solve on the
+ *               next level, prolongate, RM, post-smoother, RM.
+ *   smooth      Alg. BJ (block Jacobi) started from x = 0 with a fixed sweep count:
+ *               r = b - A x; x_i += omega A_ii^{-1} r_i for every cell block i.
+ *   criteria    Sec. 4.2 (convergence criteria): level 0 the user tolerance; level 1
+ *               ||r|| <= 0.1 ||r0|| or 20 iterations; level 2 ||r|| <= 0.5 ||r0|| or 2
+ *               iterations; deeper levels one iteration per visit; the last level of the
+ *               hierarchy is solved directly.
+ * Readings where the paper is silent:
+ *   - R = P^T, A_{l+1} = P^T A_l P (Galerkin) with P the exact injection of nested
+ *     polynomial spaces (given as 2^d constant child matrices);
+ *   - a second MGS pass when the orthogonalised norm drops below half of ||A z||;
+ *   - a correction whose orthogonalised norm is <= 1e-14 ||A z|| (or not finite) is
+ *     discarded (no append, no update);
+ *   - the coarsest system is solved with a dense LU factorisation (partial pivoting);
+ *   - restart: Alg. 2 never clears W, Z inside one call, and in floating point the
+ *     recursive residual r = r0 - W alpha drifts from b - A x as A Z = W degrades with
+ *     the basis length.  Before an RM call on a level whose basis holds lmax vectors
+ *     (lmax > 0), and on level 0 whenever the recursive residual meets the tolerance, the
+ *     level restarts: x0 := x, r0 := b - A x (true residual), W, Z := {}.  The true
+ *     residual stays monotone; the top-level stopping test is taken on it.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MAXLEV 16
+
+enum { ORC_OK = 0, ORC_NOT_CONVERGED = 1, ORC_BREAKDOWN = 2, ORC_NONFINITE = 3,
+       ORC_SINGULAR = 4, ORC_INVALID_ARG = 5 };
+
+typedef struct {
+    int n[3];        /* cells per direction (n[2] = 1 in 2-D) */
+    int ncell;
+    int *nbr;        /* [ncell][2*dim]: -e0, +e0, -e1, +e1, -e2, +e2; -1 = none */
+    double *blk;     /* [ncell][S][np][np], slot 0 = diagonal, slot s>0 = nbr[s-1] */
+    double *inv;     /* [ncell][np][np] inverse of the diagonal block */
+    /* per-level Alg. 2 state */
+    int lcap, l;
+    double *W, *Z;   /* [lcap][N] stored orthonormal basis and its search directions */
+    double *alpha;   /* [lcap] */
+    double *x0, *r0, *x, *r, *z, *w, *t, *bc, *xc;
+} olevel;
+
+typedef struct {
+    int dim, np, S, nlev, nchild;
+    olevel lv[ORC_MAXLEV];
+    double *P;       /* [nchild][np][np] */
+    double omega;
+    int sweeps;
+    double lvl_rtol[ORC_MAXLEV];
+    int lvl_maxit[ORC_MAXLEV];
+    int Nc;
+    double *Lc;      /* [Nc][Nc] packed LU factors of the coarsest operator */
+    int *piv;        /* [Nc] row interchanges of the LU factorisation */
+    /* solve bookkeeping */
+    double *hist; int *hist_type; int hist_cap, hist_len;
+    int level_iters[ORC_MAXLEV];
+    int breakdowns_in_row, status_flag;
+    int lmax, restarts;
+    double res0;     /* ||b - A x0|| of the top-level solve */
+} osolver;
+
+static double dot(int n, const double *a, const double *b) {
+    double s = 0.0;
+    for (int i = 0; i < n; i++) s += a[i] * b[i];
+    return s;
+}
+
+static int ndof(const osolver *S, int lev) { return S->lv[lev].ncell * S->np; }
+
+/* y = A x on level lev (block row K: sum over slots of blk[K][s] x[nbr]) */
+static void apply(const osolver *S, int lev, const double *x, double *y) {
+    const olevel *L = &S->lv[lev];
+    int np = S->np, nf = 2 * S->dim;
+    for (int K = 0; K < L->ncell; K++) {
+        for (int i = 0; i < np; i++) {
+            double s = 0.0;
+            for (int sl = 0; sl < S->S; sl++) {
+                int J = (sl == 0) ? K : L->nbr[K * nf + sl - 1];
+                if (J < 0) continue;
+                const double *B = L->blk + ((size_t)K * S->S + sl) * np * np;
+                for (int j = 0; j < np; j++) s += B[i * np + j] * x[(size_t)J * np + j];
+            }
+            y[(size_t)K * np + i] = s;
+        }
+    }
+}
+
+/* Alg. BJ from x^(0) = 0 with S->sweeps iterations (no norm test inside MG). */
+static void smooth(osolver *S, int lev, const double *b, double *x) {
+    olevel *L = &S->lv[lev];
+    int np = S->np, N = ndof(S, lev);
+    double *r = L->t;
+    for (int i = 0; i < N; i++) x[i] = 0.0;
+    for (int k = 0; k < S->sweeps; k++) {
+        apply(S, lev, x, r);
+        for (int i = 0; i < N; i++) r[i] = b[i] - r[i];
+        for (int K = 0; K < L->ncell; K++) {
+            const double *D = L->inv + (size_t)K * np * np;
+            for (int i = 0; i < np; i++) {
+                double dx = 0.0;
+                for (int j = 0; j < np; j++) dx += D[i * np + j] * r[(size_t)K * np + j];
+                x[(size_t)K * np + i] += S->omega * dx;
+            }
+        }
+    }
+}
+
+/* child index and parent of fine cell K on level lev */
+static void cell_coords(const olevel *L, int K, int c[3]) {
+    c[0] = K % L->n[0];
+    c[1] = (K / L->n[0]) % L->n[1];
+    c[2] = K / (L->n[0] * L->n[1]);
+}
+static int parent_of(const osolver *S, int lev, int K, int *child) {
+    int c[3];
+    cell_coords(&S->lv[lev], K, c);
+    const olevel *C = &S->lv[lev + 1];
+    int k = 0;
+    for (int j = 0; j < S->dim; j++) k |= (c[j] & 1) << j;
+    *child = k;
+    int pc[3] = {c[0] / 2, c[1] / 2, S->dim == 3 ? c[2] / 2 : 0};
+    return pc[0] + C->n[0] * (pc[1] + C->n[1] * pc[2]);
+}
+
+/* r_c = P^T r : coarse cell J gets sum over children k of P_k^T r[child] */
+static void restrict_(const osolver *S, int lev, const double *rf, double *rc) {
+    int np = S->np;
+    memset(rc, 0, sizeof(double) * ndof(S, lev + 1));
+    for (int K = 0; K < S->lv[lev].ncell; K++) {
+        int k, J = parent_of(S, lev, K, &k);
+        const double *Pk = S->P + (size_t)k * np * np;
+        for (int i = 0; i < np; i++) {
+            double s = 0.0;
+            for (int a = 0; a < np; a++) s += Pk[a * np + i] * rf[(size_t)K * np + a];
+            rc[(size_t)J * np + i] += s;
+        }
+    }
+}
+
+/* z = P z_c : child k of coarse cell J gets P_k z_c[J] */
+static void prolong(const osolver *S, int lev, const double *zc, double *zf) {
+    int np = S->np;
+    for (int K = 0; K < S->lv[lev].ncell; K++) {
+        int k, J = parent_of(S, lev, K, &k);
+        const double *Pk = S->P + (size_t)k * np * np;
+        for (int a = 0; a < np; a++) {
+            double s = 0.0;
+            for (int i = 0; i < np; i++) s += Pk[a * np + i] * zc[(size_t)J * np + i];
+            zf[(size_t)K * np + a] = s;
+        }
+    }
+}
+
+/* Gauss-Jordan inverse with partial pivoting of an np x np block; 0 on success */
+static int invert_block(int n, const double *A, double *Ainv) {
+    double *M = malloc(sizeof(double) * n * 2 * n);
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < 2 * n; j++)
+            M[i * 2 * n + j] = (j < n) ? A[i * n + j] : (j - n == i ? 1.0 : 0.0);
+    for (int c = 0; c < n; c++) {
+        int piv = c;
+        for (int i = c + 1; i < n; i++)
+            if (fabs(M[i * 2 * n + c]) > fabs(M[piv * 2 * n + c])) piv = i;
+        if (M[piv * 2 * n + c] == 0.0) { free(M); return 1; }
+        if (piv != c)
+            for (int j = 0; j < 2 * n; j++) {
+                double t = M[c * 2 * n + j]; M[c * 2 * n + j] = M[piv * 2 * n + j]; M[piv * 2 * n + j] = t;
+            }
+        double d = M[c * 2 * n + c];
+        for (int j = 0; j < 2 * n; j++) M[c * 2 * n + j] /= d;
+        for (int i = 0; i < n; i++) {
+            if (i == c) continue;
+            double f = M[i * 2 * n + c];
+            for (int j = 0; j < 2 * n; j++) M[i * 2 * n + j] -= f * M[c * 2 * n + j];
+        }
+    }
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) Ainv[i * n + j] = M[i * 2 * n + n + j];
+    free(M);
+    return 0;
+}
+
+/* Galerkin coarse operator A_{lev+1} = P^T A_lev P, formed block by block */
+static void galerkin(osolver *S, int lev) {
+    olevel *F = &S->lv[lev], *C = &S->lv[lev + 1];
+    int np = S->np, nf = 2 * S->dim, Sl = S->S;
+    size_t bs = (size_t)np * np;
+    C->blk = calloc((size_t)C->ncell * Sl * bs, sizeof(double));
+    double *tmp = malloc(sizeof(double) * bs);
+    for (int K = 0; K < F->ncell; K++) {
+        int k, J = parent_of(S, lev, K, &k);
+        for (int sl = 0; sl < Sl; sl++) {
+            int K2 = (sl == 0) ? K : F->nbr[K * nf + sl - 1];
+            if (K2 < 0) continue;
+            int k2, J2 = parent_of(S, lev, K2, &k2);
+            int cs = (J2 == J) ? 0 : sl;   /* crossing a coarse face keeps the direction */
+            const double *Ab = F->blk + ((size_t)K * Sl + sl) * bs;
+            const double *Pk = S->P + (size_t)k * bs, *Pk2 = S->P + (size_t)k2 * bs;
+            /* tmp = A_b P_k2 ; C[J][cs] += P_k^T tmp */
+            for (int a = 0; a < np; a++)
+                for (int j = 0; j < np; j++) {
+                    double s = 0.0;
+                    for (int m = 0; m < np; m++) s += Ab[a * np + m] * Pk2[m * np + j];
+                    tmp[a * np + j] = s;
+                }
+            double *Cb = C->blk + ((size_t)J * Sl + cs) * bs;
+            for (int i = 0; i < np; i++)
+                for (int j = 0; j < np; j++) {
+                    double s = 0.0;
+                    for (int a = 0; a < np; a++) s += Pk[a * np + i] * tmp[a * np + j];
+                    Cb[i * np + j] += s;
+                }
+        }
+    }
+    free(tmp);
+}
+
+static void build_nbr(osolver *S, olevel *L) {
+    int nf = 2 * S->dim;
+    L->nbr = malloc(sizeof(int) * L->ncell * nf);
+    for (int K = 0; K < L->ncell; K++) {
+        int c[3];
+        cell_coords(L, K, c);
+        int stride[3] = {1, L->n[0], L->n[0] * L->n[1]};
+        for (int j = 0; j < S->dim; j++) {
+            L->nbr[K * nf + 2 * j] = (c[j] > 0) ? K - stride[j] : -1;
+            L->nbr[K * nf + 2 * j + 1] = (c[j] < L->n[j] - 1) ? K + stride[j] : -1;
+        }
+    }
+}
+
+static void alloc_work(osolver *S, olevel *L) {
+    size_t N = (size_t)L->ncell * S->np;
+    double **v[] = {&L->x0, &L->r0, &L->x, &L->r, &L->z, &L->w, &L->t, &L->bc, &L->xc};
+    for (int i = 0; i < 9; i++) *v[i] = calloc(N, sizeof(double));
+    L->lcap = 0; L->l = 0; L->W = L->Z = L->alpha = NULL;
+}
+
+/* dense LU factorisation with partial pivoting, P A = L U, of the coarsest operator
+   (A^T for the adjoint solver is not symmetric in general); 0 on success */
+static int coarse_factor(osolver *S) {
+    olevel *L = &S->lv[S->nlev - 1];
+    int np = S->np, nf = 2 * S->dim, n = L->ncell * np;
+    S->Nc = n;
+    double *A = calloc((size_t)n * n, sizeof(double));
+    S->piv = malloc(sizeof(int) * n);
+    for (int K = 0; K < L->ncell; K++)
+        for (int sl = 0; sl < S->S; sl++) {
+            int J = (sl == 0) ? K : L->nbr[K * nf + sl - 1];
+            if (J < 0) continue;
+            const double *B = L->blk + ((size_t)K * S->S + sl) * np * np;
+            for (int i = 0; i < np; i++)
+                for (int j = 0; j < np; j++) A[(size_t)(K * np + i) * n + J * np + j] += B[i * np + j];
+        }
+    S->Lc = A;
+    for (int c = 0; c < n; c++) {
+        int p = c;
+        for (int i = c + 1; i < n; i++)
+            if (fabs(A[(size_t)i * n + c]) > fabs(A[(size_t)p * n + c])) p = i;
+        S->piv[c] = p;
+        if (A[(size_t)p * n + c] == 0.0) return 1;
+        if (p != c)
+            for (int j = 0; j < n; j++) {
+                double t = A[(size_t)c * n + j]; A[(size_t)c * n + j] = A[(size_t)p * n + j]; A[(size_t)p * n + j] = t;
+            }
+        for (int i = c + 1; i < n; i++) {
+            double f = A[(size_t)i * n + c] / A[(size_t)c * n + c];
+            A[(size_t)i * n + c] = f;
+            for (int j = c + 1; j < n; j++) A[(size_t)i * n + j] -= f * A[(size_t)c * n + j];
+        }
+    }
+    return 0;
+}
+
+static void coarse_solve(const osolver *S, const double *r, double *z) {
+    int n = S->Nc;
+    const double *A = S->Lc;
+    for (int i = 0; i < n; i++) z[i] = r[i];
+    for (int c = 0; c < n; c++)                             /* apply the row swaps */
+        if (S->piv[c] != c) { double t = z[c]; z[c] = z[S->piv[c]]; z[S->piv[c]] = t; }
+    for (int i = 0; i < n; i++)                             /* L y = P r (unit diagonal) */
+        for (int k = 0; k < i; k++) z[i] -= A[(size_t)i * n + k] * z[k];
+    for (int i = n - 1; i >= 0; i--) {                      /* U z = y */
+        for (int k = i + 1; k < n; k++) z[i] -= A[(size_t)i * n + k] * z[k];
+        z[i] /= A[(size_t)i * n + i];
+    }
+}
+
+/* ------------------------------------------------------------------------ Alg. 1 */
+static void ensure_cap(osolver *S, olevel *L) {
+    if (L->l < L->lcap) return;
+    size_t N = (size_t)L->ncell * S->np;
+    int nc = L->lcap ? 2 * L->lcap : 16;
+    L->W = realloc(L->W, sizeof(double) * N * nc);
+    L->Z = realloc(L->Z, sizeof(double) * N * nc);
+    L->alpha = realloc(L->alpha, sizeof(double) * nc);
+    L->lcap = nc;
+}
+
+/* RM(A, r0, z, W, Z) on level lev; z is overwritten.  Returns 0 if the correction was
+   appended, 1 if it was discarded (breakdown), 2 if a non-finite value appeared. */
+static int rm_step(osolver *S, int lev, double *z) {
+    olevel *L = &S->lv[lev];
+    int N = ndof(S, lev);
+    double *w = L->w;
+    apply(S, lev, z, w);                                   /* w_{l+1} := A z */
+    double naz = sqrt(dot(N, w, w));
+    if (!isfinite(naz)) return 2;
+    for (int pass = 0; pass < 2; pass++) {
+        double before = (pass == 0) ? naz : sqrt(dot(N, w, w));
+        for (int i = 0; i < L->l; i++) {                   /* for all columns w_i of W */
+            const double *Wi = L->W + (size_t)i * N, *Zi = L->Z + (size_t)i * N;
+            double beta = dot(N, Wi, w);                   /* beta := w_i . w_{l+1} */
+            for (int k = 0; k < N; k++) w[k] -= beta * Wi[k];
+            for (int k = 0; k < N; k++) z[k] -= beta * Zi[k];
+        }
+        if (sqrt(dot(N, w, w)) >= 0.5 * before) break;    /* second pass only if needed */
+    }
+    double nw = sqrt(dot(N, w, w));
+    if (!isfinite(nw)) return 2;
+    if (!(nw > 1e-14 * naz)) return 1;
+    double gamma = 1.0 / nw;                               /* gamma := 1/||w_{l+1}|| */
+    ensure_cap(S, L);
+    double *Wl = L->W + (size_t)L->l * N, *Zl = L->Z + (size_t)L->l * N;
+    for (int k = 0; k < N; k++) { Wl[k] = gamma * w[k]; Zl[k] = gamma * z[k]; }
+    L->alpha[L->l] = dot(N, Wl, L->r0);                    /* alpha_{l+1} := w_{l+1} . r0 */
+    L->l++;
+    for (int k = 0; k < N; k++) {                          /* x := x0 + Z alpha; r := r0 - W alpha */
+        double xs = L->x0[k], rs = L->r0[k];
+        for (int i = 0; i < L->l; i++) {
+            xs += L->alpha[i] * L->Z[(size_t)i * N + k];
+            rs -= L->alpha[i] * L->W[(size_t)i * N + k];
+        }
+        L->x[k] = xs; L->r[k] = rs;
+    }
+    return 0;
+}
+
+static void record(osolver *S, int lev, int type) {
+    if (lev != 0 || !S->hist || S->hist_len >= S->hist_cap) return;
+    int N = ndof(S, 0);
+    S->hist[S->hist_len] = sqrt(dot(N, S->lv[0].r, S->lv[0].r));
+    S->hist_type[S->hist_len] = type;
+    S->hist_len++;
+}
+
+/* x0 := x, r0 := b - A x, W, Z := {} on level lev (see "restart" above) */
+static void restart(osolver *S, int lev, const double *b) {
+    olevel *L = &S->lv[lev];
+    int N = ndof(S, lev);
+    apply(S, lev, L->x, L->r0);
+    for (int k = 0; k < N; k++) { L->r0[k] = b[k] - L->r0[k]; L->r[k] = L->r0[k]; L->x0[k] = L->x[k]; }
+    L->l = 0;
+    if (lev == 0) S->restarts++;
+    record(S, lev, 4);
+}
+
+/* one RM call inside MG with the level-0 breakdown bookkeeping */
+static void mg_rm(osolver *S, int lev, const double *b, double *z, int type) {
+    if (S->lmax > 0 && S->lv[lev].l >= S->lmax) restart(S, lev, b);
+    int rc = rm_step(S, lev, z);
+    if (rc == 2) S->status_flag = ORC_NONFINITE;
+    if (lev == 0) {
+        S->breakdowns_in_row = (rc == 1) ? S->breakdowns_in_row + 1 : 0;
+        if (S->breakdowns_in_row >= 2 && S->status_flag == ORC_OK) S->status_flag = ORC_BREAKDOWN;
+    }
+    record(S, lev, type);
+}
+
+/* ------------------------------------------------------------------------ Alg. 2 */
+/* x := MG(A_lev, b, x0); on entry x holds x0.  eps0/maxit0 apply to level 0. */
+static void mg(osolver *S, int lev, const double *b, double *x, double rtol0, double atol0,
+               int maxit0) {
+    olevel *L = &S->lv[lev];
+    int N = ndof(S, lev);
+    L->l = 0;                                                 /* Z := {}, W := {} */
+    apply(S, lev, x, L->r0);                                  /* r0 := b - A x0 */
+    for (int k = 0; k < N; k++) { L->r0[k] = b[k] - L->r0[k]; L->r[k] = L->r0[k]; L->x0[k] = x[k]; L->x[k] = x[k]; }
+    double n0 = sqrt(dot(N, L->r0, L->r0));
+    if (lev == 0) S->res0 = n0;
+    double eps = (lev == 0) ? fmax(rtol0 * n0, atol0) : S->lvl_rtol[lev] * n0;
+    int maxit = (lev == 0) ? maxit0 : S->lvl_maxit[lev];
+    record(S, lev, 0);
+    int it = 0;
+    for (;;) {
+        if (!(sqrt(dot(N, L->r, L->r)) > eps)) {
+            if (lev != 0 || L->l == 0) break;                 /* level 0: confirm on b - A x */
+            restart(S, lev, b);
+            if (!(sqrt(dot(N, L->r, L->r)) > eps)) break;
+        }
+        if (it >= maxit || S->status_flag != ORC_OK) break;
+        smooth(S, lev, L->r, L->z);                           /* pre-smoother */
+        mg_rm(S, lev, b, L->z, 1);
+        restrict_(S, lev, L->r, S->lv[lev + 1].bc);           /* r_c := R r */
+        olevel *C = &S->lv[lev + 1];
+        if (lev + 1 == S->nlev - 1) {
+            coarse_solve(S, C->bc, C->xc);                    /* z_c := A_c \ r_c */
+        } else {
+            memset(C->xc, 0, sizeof(double) * ndof(S, lev + 1));
+            mg(S, lev + 1, C->bc, C->xc, 0, 0, 0);            /* z_c := MG(A_c, r_c, 0) */
+        }
+        prolong(S, lev, C->xc, L->z);                         /* z := P z_c */
+        mg_rm(S, lev, b, L->z, 2);
+        smooth(S, lev, L->r, L->z);                           /* post-smoother */
+        mg_rm(S, lev, b, L->z, 3);
+        it++;
+        S->level_iters[lev]++;
+    }
+    memcpy(x, L->x, sizeof(double) * N);
+}
+
+/* ------------------------------------------------------------------------ C interface */
+void orc_destroy(void *h);
+
+/* blocks: [S][C][np][np] (slot-major input layout); nbr: [C][2d] or NULL (derived).
+   transpose != 0 builds the solver of A^T (slot s of K := (slot opp(s) of nbr)^T). */
+void *orc_create(int dim, int np, const int *n, int nlevels, const double *blocks,
+                 const double *P, double omega, int sweeps, const double *lvl_rtol,
+                 const int *lvl_maxit, int lmax, int transpose, int *status) {
+    *status = ORC_INVALID_ARG;
+    if (dim < 2 || dim > 3 || np < 1 || nlevels < 2 || nlevels > ORC_MAXLEV) return NULL;
+    for (int j = 0; j < dim; j++)
+        if (n[j] <= 0 || n[j] % (1 << (nlevels - 1))) return NULL;
+    osolver *S = calloc(1, sizeof(osolver));
+    S->dim = dim; S->np = np; S->S = 2 * dim + 1; S->nlev = nlevels; S->nchild = 1 << dim;
+    S->omega = omega; S->sweeps = sweeps; S->lmax = lmax;
+    for (int l = 0; l < nlevels; l++) { S->lvl_rtol[l] = lvl_rtol[l]; S->lvl_maxit[l] = lvl_maxit[l]; }
+    size_t bs = (size_t)np * np;
+    S->P = malloc(sizeof(double) * S->nchild * bs);
+    memcpy(S->P, P, sizeof(double) * S->nchild * bs);
+    for (int l = 0; l < nlevels; l++) {
+        olevel *L = &S->lv[l];
+        L->n[0] = n[0] >> l; L->n[1] = n[1] >> l; L->n[2] = dim == 3 ? n[2] >> l : 1;
+        L->ncell = L->n[0] * L->n[1] * L->n[2];
+        build_nbr(S, L);
+        alloc_work(S, L);
+    }
+    olevel *F = &S->lv[0];
+    int nf = 2 * dim;
+    F->blk = malloc(sizeof(double) * F->ncell * S->S * bs);
+    for (int K = 0; K < F->ncell; K++)
+        for (int sl = 0; sl < S->S; sl++) {
+            double *dst = F->blk + ((size_t)K * S->S + sl) * bs;
+            if (!transpose) {
+                memcpy(dst, blocks + ((size_t)sl * F->ncell + K) * bs, sizeof(double) * bs);
+            } else {
+                int J = (sl == 0) ? K : F->nbr[K * nf + sl - 1];
+                int opp = (sl == 0) ? 0 : (((sl - 1) ^ 1) + 1);
+                if (J < 0) { memset(dst, 0, sizeof(double) * bs); continue; }
+                const double *src = blocks + ((size_t)opp * F->ncell + J) * bs;
+                for (int i = 0; i < np; i++)
+                    for (int j = 0; j < np; j++) dst[i * np + j] = src[j * np + i];
+            }
+        }
+    for (int l = 0; l + 1 < nlevels; l++) galerkin(S, l);
+    for (int l = 0; l < nlevels; l++) {
+        olevel *L = &S->lv[l];
+        L->inv = malloc(sizeof(double) * L->ncell * bs);
+        for (int K = 0; K < L->ncell; K++)
+            if (invert_block(np, L->blk + (size_t)K * S->S * bs, L->inv + (size_t)K * bs)) {
+                *status = ORC_SINGULAR; orc_destroy(S); return NULL;
+            }
+    }
+    if (coarse_factor(S)) { *status = ORC_SINGULAR; orc_destroy(S); return NULL; }
+    *status = ORC_OK;
+    return S;
+}
+
+void orc_destroy(void *h) {
+    osolver *S = h;
+    if (!S) return;
+    for (int l = 0; l < S->nlev; l++) {
+        olevel *L = &S->lv[l];
+        void *p[] = {L->nbr, L->blk, L->inv, L->W, L->Z, L->alpha, L->x0, L->r0, L->x, L->r,
+                     L->z, L->w, L->t, L->bc, L->xc};
+        for (int i = 0; i < 15; i++) free(p[i]);
+    }
+    free(S->P); free(S->Lc); free(S->piv); free(S);
+}
+
+/* Solve A x = b to ||r|| <= max(rtol ||b - A x0||, atol).  x: in x0, out x.
+   hist/hist_type (capacity hist_cap) receive ||r|| after each level-0 RM with type
+   0 initial, 1 pre-smoother, 2 coarse correction, 3 post-smoother, 4 restart (true
+   residual). */
+int orc_solve(void *h, const double *b, double *x, double rtol, double atol, int maxiter,
+              double *hist, int *hist_type, int hist_cap, int *hist_len, int *iters,
+              double *rel_res, int *level_iters) {
+    osolver *S = h;
+    int N = ndof(S, 0);
+    for (int k = 0; k < N; k++)
+        if (!isfinite(b[k]) || !isfinite(x[k])) return ORC_NONFINITE;
+    S->hist = hist; S->hist_type = hist_type; S->hist_cap = hist ? hist_cap : 0; S->hist_len = 0;
+    memset(S->level_iters, 0, sizeof(S->level_iters));
+    S->breakdowns_in_row = 0; S->status_flag = ORC_OK; S->restarts = 0;
+    mg(S, 0, b, x, rtol, atol, maxiter);
+    olevel *L = &S->lv[0];
+    apply(S, 0, x, L->t);                                     /* report the true residual */
+    for (int k = 0; k < N; k++) L->t[k] = b[k] - L->t[k];
+    double n0 = S->res0, nr = sqrt(dot(N, L->t, L->t));
+    if (hist_len) *hist_len = S->hist_len;
+    if (iters) *iters = S->level_iters[0];
+    if (rel_res) *rel_res = (n0 > 0) ? nr / n0 : 0.0;
+    if (level_iters) memcpy(level_iters, S->level_iters, sizeof(int) * S->nlev);
+    if (S->status_flag != ORC_OK) return S->status_flag;
+    return (nr <= fmax(rtol * n0, atol)) ? ORC_OK : ORC_NOT_CONVERGED;
+}
+
+/* component access for the tests */
+int orc_ncell(void *h, int lev) { return ((osolver *)h)->lv[lev].ncell; }
+void orc_apply(void *h, int lev, const double *x, double *y) { apply(h, lev, x, y); }
+void orc_smooth(void *h, int lev, const double *b, double *x) { smooth(h, lev, b, x); }
+void orc_restrict(void *h, int lev, const double *rf, double *rc) { restrict_(h, lev, rf, rc); }
+void orc_prolong(void *h, int lev, const double *zc, double *zf) { prolong(h, lev, zc, zf); }
+void orc_coarse_solve(void *h, const double *r, double *z) { coarse_solve(h, r, z); }
+/* blocks of level lev in the input layout [S][C][np][np] */
+void orc_get_blocks(void *h, int lev, double *out) {
+    osolver *S = h;
+    olevel *L = &S->lv[lev];
+    size_t bs = (size_t)S->np * S->np;
+    for (int K = 0; K < L->ncell; K++)
+        for (int sl = 0; sl < S->S; sl++)
+            memcpy(out + ((size_t)sl * L->ncell + K) * bs, L->blk + ((size_t)K * S->S + sl) * bs,
+                   sizeof(double) * bs);
+}
+void orc_get_inv(void *h, int lev, double *out) {
+    osolver *S = h;
+    memcpy(out, S->lv[lev].inv, sizeof(double) * S->lv[lev].ncell * S->np * S->np);
+}
+
+/* RM driver on level lev: start a fresh basis with x0 and r0 = b - A x0 */
+void orc_rm_begin(void *h, int lev, const double *b, const double *x0) {
+    osolver *S = h;
+    olevel *L = &S->lv[lev];
+    int N = ndof(S, lev);
+    L->l = 0;
+    apply(S, lev, x0, L->r0);
+    for (int k = 0; k < N; k++) { L->r0[k] = b[k] - L->r0[k]; L->r[k] = L->r0[k]; L->x0[k] = x0[k]; L->x[k] = x0[k]; }
+}
+/* one Alg. 1 call with correction z (copied); returns rm_step's code; x, r, l out */
+int orc_rm_call(void *h, int lev, const double *z, double *x, double *r, int *l) {
+    osolver *S = h;
+    olevel *L = &S->lv[lev];
+    int N = ndof(S, lev);
+    memcpy(L->z, z, sizeof(double) * N);
+    int rc = rm_step(S, lev, L->z);
+    memcpy(x, L->x, sizeof(double) * N);
+    memcpy(r, L->r, sizeof(double) * N);
+    *l = L->l;
+    return rc;
+}
+void orc_rm_basis(void *h, int lev, double *W, double *Z) {
+    osolver *S = h;
+    olevel *L = &S->lv[lev];
+    size_t N = (size_t)ndof(S, lev);
+    memcpy(W, L->W, sizeof(double) * N * L->l);
+    memcpy(Z, L->Z, sizeof(double) * N * L->l);
+}
+
+/* ------------------------------------------------------------------------ adjoint gradient */
+/* g_K = -lambda^T (dA/d log nu_K) u for A = sum_K nu_K V + sum_F gamma_F F_F +
+   sum_{bnd F} nu_K B_F, gamma_F = 2 nu_K nu_K' / (nu_K + nu_K').
+   V [np][np]; F [dim][4][np][np] (LL, LR, RL, RR; L = low-side cell); B [dim][2][np][np]. */
+static double bil(int np, const double *M, const double *l, const double *u) {
+    double s = 0.0;
+    for (int i = 0; i < np; i++)
+        for (int j = 0; j < np; j++) s += l[i] * M[i * np + j] * u[j];
+    return s;
+}
+void orc_grad_lognu(int dim, int np, const int *n, const double *nu, const double *V,
+                    const double *F, const double *B, const double *lam, const double *u,
+                    double *g) {
+    int C = n[0] * n[1] * (dim == 3 ? n[2] : 1);
+    int stride[3] = {1, n[0], n[0] * n[1]};
+    size_t bs = (size_t)np * np;
+    for (int K = 0; K < C; K++) {
+        int c[3] = {K % n[0], (K / n[0]) % n[1], dim == 3 ? K / (n[0] * n[1]) : 0};
+        const double *lK = lam + (size_t)K * np, *uK = u + (size_t)K * np;
+        double s = bil(np, V, lK, uK);                       /* d(nu_K V)/d nu_K */
+        for (int k = 0; k < dim; k++) {
+            const double *Fk = F + (size_t)k * 4 * bs, *Bk = B + (size_t)k * 2 * bs;
+            /* high face of K: K is the low-side cell L, neighbour R */
+            if (c[k] < n[k] - 1) {
+                int R = K + stride[k];
+                double a = nu[K], b = nu[R], dg = 2.0 * b * b / ((a + b) * (a + b));
+                const double *lR = lam + (size_t)R * np, *uR = u + (size_t)R * np;
+                s += dg * (bil(np, Fk, lK, uK) + bil(np, Fk + bs, lK, uR) +
+                           bil(np, Fk + 2 * bs, lR, uK) + bil(np, Fk + 3 * bs, lR, uR));
+            } else {
+                s += bil(np, Bk + bs, lK, uK);
+            }
+            /* low face of K: K is the high-side cell R, neighbour L */
+            if (c[k] > 0) {
+                int Lc = K - stride[k];
+                double a = nu[K], b = nu[Lc], dg = 2.0 * b * b / ((a + b) * (a + b));
+                const double *lL = lam + (size_t)Lc * np, *uL = u + (size_t)Lc * np;
+                s += dg * (bil(np, Fk, lL, uL) + bil(np, Fk + bs, lL, uK) +
+                           bil(np, Fk + 2 * bs, lK, uL) + bil(np, Fk + 3 * bs, lK, uK));
+            } else {
+                s += bil(np, Bk, lK, uK);
+            }
+        }
+        g[K] = -nu[K] * s;
+    }
+}
+
+/* number of stored basis vectors on level lev (after a solve: of its last MG call) */
+int orc_basis_size(void *h, int lev) { return ((osolver *)h)->lv[lev].l; }
+int orc_restarts(void *h) { return ((osolver *)h)->restarts; }

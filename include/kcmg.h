@@ -1,0 +1,166 @@
+/*
+ * kcmg.h -- C interface of the GB300 K-cycle orthonormalization multigrid library.
+ *
+ * The library solves A x = b for a block-sparse operator A with one Np x Np block row per
+ * cell of a Cartesian grid (the per-cell local DOF blocks of a DG discretisation, Sec. 2
+ * "XDG discretization" of Toprak & Kummer) by the orthonormalization multigrid K-cycle:
+ * Alg. 2 (MG) with the residual minimisation Alg. 1 (RM) after every smoother and
+ * coarse-grid correction, the damped block-Jacobi smoother of Alg. BJ, the level-local
+ * convergence criteria of Sec. 4.2, restriction/prolongation across a 2^d cell-
+ * agglomeration hierarchy (Alg. 2, R^lambda and P^lambda) and a direct coarsest solve.
+ *
+ * Conventions shared by every call:
+ *   - Vectors are FP64, length N = ncells * np, DOF index = cell * np + mode; cells are
+ *     numbered lexicographically with x fastest.  Multi-right-hand-side vectors are
+ *     [N][nrhs] row-major (right-hand sides fastest).
+ *   - A pointer argument may be host or device memory (unified addressing tells them
+ *     apart); host data is staged through the library's own device buffers, so the
+ *     host-pointer path includes the host<->device copies.
+ *   - Every call is stream-ordered on the stream given at setup and returns after its
+ *     results are complete on that stream (solves synchronise to read their status).
+ *   - The caller owns every pointer it passes; the library never frees caller memory.
+ *     The library owns everything it allocates until kcmg_destroy.
+ *   - Errors are reported through the return value; kcmg_last_error gives a message.
+ *     After any status other than KCMG_OK or KCMG_NOT_CONVERGED the output vectors are
+ *     unspecified.  On KCMG_NOT_CONVERGED x holds the last iterate, whose true residual
+ *     is no larger than that of x0 (Alg. 2 "ENSURE" clause).
+ *   - Calls on one context must not overlap (one host thread at a time).
+ */
+#ifndef KCMG_H
+#define KCMG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KCMG_MAX_LEVELS 12
+
+typedef struct kcmg_ctx kcmg_ctx;
+
+typedef enum {
+    KCMG_OK = 0,             /* converged to the requested tolerance */
+    KCMG_NOT_CONVERGED = 1,  /* maxiter reached; x is the best iterate */
+    KCMG_BREAKDOWN = 2,      /* two consecutive level-0 corrections were linearly dependent */
+    KCMG_NONFINITE = 3,      /* NaN/Inf in an input or in the iteration */
+    KCMG_SINGULAR = 4,       /* a diagonal block or the coarsest operator is singular */
+    KCMG_INVALID_ARG = 5,    /* bad sizes, null pointers, unsupported np, ... */
+    KCMG_OOM = 6,            /* device allocation failed */
+    KCMG_CUDA_ERROR = 7      /* a CUDA runtime call failed */
+} kcmg_status;
+
+typedef enum {
+    KCMG_FP64 = 0,         /* every kernel in FP64 */
+    KCMG_MIXED = 1,        /* smoother sweeps, transfers and every coarse level (operators,
+                              basis W/Z, residual minimisation) in FP32; level 0's residual
+                              minimisation (w = A z with the FP64 operator, W, Z, x, r), all
+                              Gram coefficients and the coarsest solve in FP64.  The FP64
+                              minimisation over FP32-computed corrections is the iterative
+                              refinement: the attainable residual is FP64's */
+    KCMG_MIXED_BF16INV = 2 /* as KCMG_MIXED with the block-Jacobi inverses stored in BF16 */
+} kcmg_precision;
+
+/* Setup input: the fine operator, the hierarchy and the smoother/cycle parameters. */
+typedef struct {
+    int dim;                 /* 2 or 3 */
+    int np;                  /* local DOFs per cell; supported: 3, 4, 6, 10, 20 */
+    int n[3];                /* cells per direction (n[2] ignored for dim 2); each divisible
+                                by 2^(nlevels-1) */
+    int nlevels;             /* >= 2; the last level is solved directly */
+    const double *blocks;    /* fine operator, [2*dim+1][ncells][np][np] row-major blocks;
+                                slot 0 = diagonal block of the cell, slot 1+2k / 2+2k = the
+                                coupling to the -e_k / +e_k face neighbour (zero where the
+                                neighbour is outside the grid).  Copied at setup. */
+    const double *prolong;   /* [2^dim][np][np]: P_k maps coarse modes to the modes of child
+                                k = cx + 2 cy + 4 cz of an agglomerated cell; the same P_k on
+                                every level.  R = P^T; coarse operators are P^T A P. */
+    double omega;            /* block-Jacobi damping (Alg. BJ) */
+    int sweeps;              /* block-Jacobi sweeps per smoother call, from x = 0 */
+    double lvl_rtol[KCMG_MAX_LEVELS];  /* levels >= 1: stop when ||r|| <= rtol ||r0||   */
+    int lvl_maxit[KCMG_MAX_LEVELS];    /* levels >= 1: ... or after maxit iterations     */
+                                       /* (Sec. 4.2: 0.1/20, 0.5/2, then 0/1)           */
+    int lmax;                /* restart a level when its basis would exceed lmax vectors
+                                (0 = only when the device capacity is reached) */
+    int precision;           /* kcmg_precision */
+    int use_graph;           /* 1: run the cycle as a CUDA graph with conditional while
+                                nodes; 0: host-driven control (reads a flag per loop test) */
+} kcmg_params;
+
+/* Fill p with the defaults of Sec. 4.2 / Alg. BJ for the given sizes (blocks, prolong
+   must still be set). */
+void kcmg_default_params(kcmg_params *p, int dim, int np, const int n[3], int nlevels);
+
+/* Convergence report.  hist/hist_type are caller-owned arrays of length hist_cap (may be
+   NULL): ||r|| after every level-0 RM call with type 0 initial, 1 pre-smoother, 2 coarse
+   correction, 3 post-smoother, 4 restart (true residual replaces the recursive one). */
+typedef struct {
+    int iters;                          /* level-0 cycles */
+    int level_iters[KCMG_MAX_LEVELS];   /* cycles per level, summed over visits */
+    int restarts;                       /* level-0 restarts */
+    int refinements;                    /* mixed forms: FP64 true-residual evaluations on
+                                           level 0 (restarts + 1), i.e. refinement steps */
+    double res0;                        /* ||b - A x0|| */
+    double rel_res;                     /* ||b - A x|| / res0, FP64 true residual */
+    int hist_cap, hist_len;
+    double *hist;
+    int *hist_type;
+} kcmg_info;
+
+/* Build the hierarchy on the device: copies blocks and prolong, forms the Galerkin
+   operators A_{l+1} = P^T A_l P, inverts every diagonal block, inverts the coarsest
+   operator densely, and lays out the FP64 (and for mixed precision FP32/BF16) copies
+   for the kernels.  cuda_stream: a cudaStream_t (NULL = default stream); every call
+   orders the library's own stream after it.  *out receives a context even on failure,
+   so that kcmg_last_error can explain the failure: destroy it in every case. */
+kcmg_status kcmg_setup(kcmg_ctx **out, const kcmg_params *p, void *cuda_stream);
+
+/* Solve A x = b (Alg. 2 at level 0) until ||b - A x|| <= max(rtol ||b - A x0||, atol)
+   or maxiter level-0 cycles.  x: in x0, out x.  nrhs must be 1. info may be NULL. */
+kcmg_status kcmg_solve(kcmg_ctx *ctx, const double *b, double *x, int nrhs, double rtol,
+                       double atol, int maxiter, kcmg_info *info);
+
+/* Solve A^T lambda = g with the same cycle on the transposed hierarchy (built at the
+   first call; shared with the forward hierarchy when A is bitwise symmetric).  Used for
+   the adjoint gradient dL/db = lambda. */
+kcmg_status kcmg_solve_adjoint(kcmg_ctx *ctx, const double *g, double *lambda, int nrhs,
+                               double rtol, double atol, int maxiter, kcmg_info *info);
+
+/* Adjoint coefficient gradient of the SWIP operator A = sum_K nu_K V + sum_F gamma_F F_F +
+   sum_{boundary F} nu_K B_F with gamma_F = 2 nu_K nu_K'/(nu_K + nu_K'):
+   g_K = -lambda^T (dA/d log nu_K) u for every cell K.
+   nu [ncells]; V [np][np]; F [dim][4][np][np] (interior face, unit gamma: LL, LR, RL, RR,
+   L = cell on the low side of the face); B [dim][2][np][np] (boundary face, unit nu: low,
+   high face of the cell); lambda, u [N]; g [ncells] out.  Uses the grid of ctx. */
+kcmg_status kcmg_grad_lognu(kcmg_ctx *ctx, const double *nu, const double *V, const double *F,
+                            const double *B, const double *lambda, const double *u, double *g);
+
+/* ---- component calls (for verification; each runs the same kernels as the solve) ---- */
+
+/* y = A_level x with the FP64 operator (op = 0) or the inner-precision operator (op = 1,
+   mixed precision only; inputs/outputs still FP64). */
+kcmg_status kcmg_apply(kcmg_ctx *ctx, int level, int op, const double *x, double *y);
+/* z = BJ_level(r) from z = 0 (Alg. BJ, omega and sweeps of setup), inner precision. */
+kcmg_status kcmg_smooth(kcmg_ctx *ctx, int level, const double *r, double *z);
+/* rc = P^T r (level -> level+1) and z = P zc (level+1 -> level), inner precision. */
+kcmg_status kcmg_restrict(kcmg_ctx *ctx, int level, const double *r, double *rc);
+kcmg_status kcmg_prolong(kcmg_ctx *ctx, int level, const double *zc, double *z);
+/* z = A_coarsest^{-1} r (FP64). */
+kcmg_status kcmg_coarse_solve(kcmg_ctx *ctx, const double *r, double *z);
+/* Galerkin blocks of a level in the setup layout [2d+1][ncells][np][np] (FP64). */
+kcmg_status kcmg_get_blocks(kcmg_ctx *ctx, int level, double *out);
+/* Alg. 1 on a level in the inner precision: start from x0 (r0 = b - A x0, empty basis),
+   then apply RM to the corrections z[0..ncorr) ([ncorr][N_level]) in turn.  Returns the
+   final x and r (recursive residual) and the basis size in *l. */
+kcmg_status kcmg_rm_sequence(kcmg_ctx *ctx, int level, const double *b, const double *x0,
+                             const double *z, int ncorr, double *x, double *r, int *l);
+
+/* Level sizes: number of cells of a level (0 if out of range). */
+int kcmg_level_cells(const kcmg_ctx *ctx, int level);
+
+const char *kcmg_last_error(const kcmg_ctx *ctx);
+const char *kcmg_status_string(kcmg_status s);
+void kcmg_destroy(kcmg_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KCMG_H */

@@ -30,10 +30,11 @@
  *   - the coarsest system is solved with a dense LU factorisation (partial pivoting);
  *   - restart: Alg. 2 never clears W, Z inside one call, and in floating point the
  *     recursive residual r = r0 - W alpha drifts from b - A x as A Z = W degrades with
- *     the basis length.  Before an RM call on a level whose basis holds lmax vectors
- *     (lmax > 0), and on level 0 whenever the recursive residual meets the tolerance, the
- *     level restarts: x0 := x, r0 := b - A x (true residual), W, Z := {}.  The true
- *     residual stays monotone; the top-level stopping test is taken on it.
+ *     the basis length.  At the end of a cycle whose basis could not take another three
+ *     vectors within lmax (lmax > 0: l + 3 > lmax), and on level 0 whenever the recursive
+ *     residual meets the tolerance, the level restarts: x0 := x, r0 := b - A x (true
+ *     residual), W, Z := {}.  The true residual stays monotone; the top-level stopping
+ *     test is taken on it.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -374,7 +375,7 @@ static void restart(osolver *S, int lev, const double *b) {
 
 /* one RM call inside MG with the level-0 breakdown bookkeeping */
 static void mg_rm(osolver *S, int lev, const double *b, double *z, int type) {
-    if (S->lmax > 0 && S->lv[lev].l >= S->lmax) restart(S, lev, b);
+    (void)b;
     int rc = rm_step(S, lev, z);
     if (rc == 2) S->status_flag = ORC_NONFINITE;
     if (lev == 0) {
@@ -422,6 +423,7 @@ static void mg(osolver *S, int lev, const double *b, double *x, double rtol0, do
         mg_rm(S, lev, b, L->z, 3);
         it++;
         S->level_iters[lev]++;
+        if (S->lmax > 0 && L->l + 3 > S->lmax) restart(S, lev, b);
     }
     memcpy(x, L->x, sizeof(double) * N);
 }

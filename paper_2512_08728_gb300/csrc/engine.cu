@@ -1,0 +1,991 @@
+// Host engine and C interface of libkcmg: device setup of the agglomeration hierarchy,
+// the K-cycle driver (Alg. 2 with Alg. 1 after every correction), FP64 iterative
+// refinement around an FP32 cycle, and the CUDA-graph form of the cycle in which every
+// level's while loop is a conditional while node driven by device-side state.
+#include "kcmg_internal.h"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+using namespace kcmg;
+
+namespace {
+
+struct Level {
+  int n[3] = {1, 1, 1};
+  int ncell = 0, N = 0, G = 0, rows_pad = 0, block_rows = 0;
+  int* nbr = nullptr;
+  double* nat = nullptr;            // natural FP64 blocks [S][C][np][np]
+  double* A64 = nullptr;            // row-interleaved FP64 operator
+  double* D64 = nullptr;            // row-interleaved FP64 block inverses
+  float* A32 = nullptr;             // mixed precision copies
+  float* D32 = nullptr;
+  __nv_bfloat16* D16 = nullptr;
+  void *x = nullptr, *r = nullptr, *b = nullptr, *z = nullptr, *t = nullptr, *w = nullptr,
+       *wre = nullptr, *W = nullptr, *Z = nullptr;
+  // mixed form, level 0 only: FP32 copies for the smoother sweeps (the level's own
+  // vectors are FP64 there)
+  float *r_lo = nullptr, *z_lo = nullptr, *t_lo = nullptr;
+  int lcap = 0;
+  int nblk = 1;                     // blocks of the vector / dot kernels
+  double *h = nullptr, *h2 = nullptr, *partial = nullptr;
+  LevelState* st = nullptr;
+};
+
+}  // namespace
+
+struct kcmg_ctx {
+  kcmg_params p{};
+  int dim = 0, np = 0, S = 0, nlev = 0, nch = 0;
+  bool mixed = false;
+  cudaStream_t user = nullptr, s = nullptr;
+  cudaStream_t cap[KCMG_MAX_LEVELS + 2] = {};
+  cudaEvent_t ev = nullptr;
+  std::vector<Level> lv;
+  double* P64 = nullptr;
+  float* P32 = nullptr;
+  double* Ainv = nullptr;
+  int Nc = 0;
+  double *ro = nullptr, *scal = nullptr;
+  double* hist = nullptr;
+  int* hist_type = nullptr;
+  int hist_cap = 4096;
+  double *stage_in = nullptr, *stage_out = nullptr, *stage_big = nullptr;
+  size_t stage_big_len = 0;
+  int* dflag = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  bool graph_ready = false;
+  kcmg_ctx* adj = nullptr;       // transposed hierarchy (may be this)
+  bool adj_built = false;
+  std::vector<void*> allocs;
+  std::string err;
+};
+
+namespace {
+
+struct Fail {
+  kcmg_status st;
+};
+
+void set_err(kcmg_ctx* c, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+}
+
+#define CK(call)                                                                     \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess) {                                                         \
+      set_err(ctx, "%s failed at %s:%d: %s", #call, __FILE__, __LINE__,              \
+              cudaGetErrorString(e_));                                               \
+      throw Fail{e_ == cudaErrorMemoryAllocation ? KCMG_OOM : KCMG_CUDA_ERROR};      \
+    }                                                                                \
+  } while (0)
+
+#define REQUIRE(cond, ...)               \
+  do {                                   \
+    if (!(cond)) {                       \
+      set_err(ctx, __VA_ARGS__);         \
+      throw Fail{KCMG_INVALID_ARG};      \
+    }                                    \
+  } while (0)
+
+template <typename T>
+T* dalloc(kcmg_ctx* ctx, size_t n) {
+  void* p = nullptr;
+  CK(cudaMalloc(&p, n * sizeof(T) + 16));
+  ctx->allocs.push_back(p);
+  return static_cast<T*>(p);
+}
+
+// copy n doubles from a host or device pointer into device memory dst (unified
+// addressing lets cudaMemcpyDefault tell host from device pointers)
+void copy_in(kcmg_ctx* ctx, double* dst, const double* src, size_t n) {
+  CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDefault, ctx->s));
+}
+void copy_out(kcmg_ctx* ctx, double* dst, const double* src, size_t n) {
+  CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDefault, ctx->s));
+}
+
+int level_cells(const int* n, int dim) { return n[0] * n[1] * (dim == 3 ? n[2] : 1); }
+
+// ------------------------------------------------------------------ setup
+void setup_level_geometry(kcmg_ctx* ctx, Level& L, int l) {
+  for (int j = 0; j < 3; ++j) L.n[j] = (j < ctx->dim) ? (ctx->p.n[j] >> l) : 1;
+  L.ncell = level_cells(L.n, ctx->dim);
+  L.N = L.ncell * ctx->np;
+  L.block_rows = block_rows_for(ctx->np);
+  L.rows_pad = ((L.N + L.block_rows - 1) / L.block_rows) * L.block_rows;
+  L.G = L.rows_pad / 32;
+  L.nblk = (L.N + kVecThreads * 4 - 1) / (kVecThreads * 4);
+  if (L.nblk > kDotBlocksMax) L.nblk = kDotBlocksMax;
+  if (L.nblk < 1) L.nblk = 1;
+  L.nbr = dalloc<int>(ctx, (size_t)L.ncell * 2 * ctx->dim);
+  launch_build_nbr(ctx->dim, L.n, L.nbr, ctx->s);
+}
+
+template <typename T>
+void alloc_cycle_vectors(kcmg_ctx* ctx, Level& L, int lcap) {
+  const size_t N = L.N;
+  L.lcap = lcap;
+  L.x = dalloc<T>(ctx, N);
+  L.r = dalloc<T>(ctx, N);
+  L.b = dalloc<T>(ctx, N);
+  L.z = dalloc<T>(ctx, N);
+  L.t = dalloc<T>(ctx, N);
+  L.w = dalloc<T>(ctx, N);
+  L.wre = dalloc<T>(ctx, N);
+  L.W = dalloc<T>(ctx, N * lcap);
+  L.Z = dalloc<T>(ctx, N * lcap);
+  L.h = dalloc<double>(ctx, lcap);
+  L.h2 = dalloc<double>(ctx, lcap);
+  const size_t spmv_blocks = L.rows_pad / L.block_rows;
+  size_t plen = (size_t)kDotBlocksMax * (lcap + 1);
+  if (spmv_blocks > plen) plen = spmv_blocks;
+  if ((size_t)4 * 65536 > plen) plen = 4 * 65536;
+  L.partial = dalloc<double>(ctx, plen);
+  L.st = dalloc<LevelState>(ctx, 1);
+  CK(cudaMemsetAsync(L.st, 0, sizeof(LevelState), ctx->s));
+}
+
+void build_hierarchy(kcmg_ctx* ctx, const double* blocks_src) {
+  const int np = ctx->np, dim = ctx->dim, S = ctx->S;
+  const size_t bs = (size_t)np * np;
+  for (int l = 0; l < ctx->nlev; ++l) setup_level_geometry(ctx, ctx->lv[l], l);
+  // fine natural blocks
+  Level& F = ctx->lv[0];
+  F.nat = dalloc<double>(ctx, (size_t)S * F.ncell * bs);
+  copy_in(ctx, F.nat, blocks_src, (size_t)S * F.ncell * bs);
+  for (int l = 0; l + 1 < ctx->nlev; ++l) {
+    Level &A = ctx->lv[l], &C = ctx->lv[l + 1];
+    C.nat = dalloc<double>(ctx, (size_t)S * C.ncell * bs);
+    if (!launch_galerkin(np, dim, A.nat, A.nbr, A.n, C.n, ctx->P64, C.nat, ctx->s))
+      REQUIRE(false, "unsupported np %d", np);
+    CK(cudaGetLastError());
+  }
+  // block inverses and interleaved copies
+  double* inv_nat = dalloc<double>(ctx, (size_t)F.ncell * bs);
+  for (int l = 0; l < ctx->nlev; ++l) {
+    Level& L = ctx->lv[l];
+    CK(cudaMemsetAsync(ctx->dflag, 0, sizeof(int), ctx->s));
+    launch_block_inverse(np, L.nat, L.ncell, inv_nat, ctx->dflag, ctx->s);
+    CK(cudaGetLastError());
+    int fail = 0;
+    CK(cudaMemcpyAsync(&fail, ctx->dflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    if (fail) {
+      set_err(ctx, "diagonal block of level %d is singular", l);
+      throw Fail{KCMG_SINGULAR};
+    }
+    const size_t opsz = (size_t)S * L.G * ((np + 1) / 2) * 64;
+    const size_t invsz = (size_t)L.G * ((np + 1) / 2) * 64;
+    L.A64 = dalloc<double>(ctx, opsz);
+    L.D64 = dalloc<double>(ctx, invsz);
+    launch_interleave<double>(np, S, L.nat, L.ncell, L.G, L.A64, ctx->s);
+    launch_interleave<double>(np, 1, inv_nat, L.ncell, L.G, L.D64, ctx->s);
+    if (ctx->mixed) {
+      L.A32 = dalloc<float>(ctx, opsz);
+      launch_interleave<float>(np, S, L.nat, L.ncell, L.G, L.A32, ctx->s);
+      if (ctx->p.precision == KCMG_MIXED_BF16INV) {
+        L.D16 = dalloc<__nv_bfloat16>(ctx, invsz);
+        launch_interleave<__nv_bfloat16>(np, 1, inv_nat, L.ncell, L.G, L.D16, ctx->s);
+      } else {
+        L.D32 = dalloc<float>(ctx, invsz);
+        launch_interleave<float>(np, 1, inv_nat, L.ncell, L.G, L.D32, ctx->s);
+      }
+    }
+    CK(cudaGetLastError());
+  }
+  // dense inverse of the coarsest operator (Gauss-Jordan with partial pivoting)
+  Level& C = ctx->lv[ctx->nlev - 1];
+  const int n = C.N;
+  ctx->Nc = n;
+  double* M = dalloc<double>(ctx, (size_t)n * 2 * n);
+  double* fcol = dalloc<double>(ctx, n);
+  launch_assemble_dense(np, dim, C.nat, C.nbr, C.ncell, M, ctx->s);
+  CK(cudaMemsetAsync(ctx->dflag, 0, sizeof(int), ctx->s));
+  for (int c = 0; c < n; ++c) launch_dense_gj_step(M, n, c, fcol, ctx->dflag, ctx->s);
+  CK(cudaGetLastError());
+  ctx->Ainv = dalloc<double>(ctx, (size_t)n * n);
+  launch_extract_inverse(M, n, ctx->Ainv, ctx->s);
+  int fail = 0;
+  CK(cudaMemcpyAsync(&fail, ctx->dflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaStreamSynchronize(ctx->s));
+  if (fail) {
+    set_err(ctx, "coarsest operator (%d DOFs) is singular", n);
+    throw Fail{KCMG_SINGULAR};
+  }
+}
+
+// ------------------------------------------------------------------ the cycle
+// Level 0 keeps its vectors, basis and residual minimisation in T0 (= FP64); every other
+// level, and the smoother sweeps and transfers of level 0, work in T.  T = double is the
+// FP64 form; T = float the mixed form, where the FP64 residual minimisation of level 0
+// over FP32-computed corrections acts as the iterative refinement.
+template <typename T0, typename T>
+struct Cycle {
+  kcmg_ctx* ctx;
+  bool capture = false;
+  cudaGraphConditionalHandle handle[KCMG_MAX_LEVELS] = {};
+
+  static constexpr bool kMixed = !std::is_same<T0, T>::value;
+
+  const T* Ainner(const Level& L) const;   // operator in T
+  const T* Pm() const;
+
+  EpiArgs epi(int lev, int kind) const {
+    Level& L = ctx->lv[lev];
+    EpiArgs e;
+    e.st = L.st;
+    e.kind = kind;
+    e.h = L.h;
+    e.h2 = L.h2;
+    if (lev == 0) {
+      e.hist = ctx->hist;
+      e.hist_type_buf = ctx->hist_type;
+    }
+    if (capture) {
+      e.use_handle = 1;
+      e.handle = handle[lev];
+    }
+    return e;
+  }
+
+  // the smoother sweeps in T on buffers z/t; returns the buffer holding the result
+  T* sweeps(const Level& L, const T* r, T* z, T* t, cudaStream_t s) {
+    T* buf[2] = {z, t};
+    const double om = ctx->p.omega;
+    const int sw = ctx->p.sweeps;
+    for (int k = 0; k < sw; ++k) {
+      T* out = buf[k & 1];
+      const T* old = buf[(k + 1) & 1];
+      if (std::is_same<T, double>::value) {
+        launch_bj_sweep<double, double>(ctx->np, ctx->dim, (const double*)Ainner(L), L.D64, L.nbr, L.N,
+                                        L.G, L.rows_pad, L.block_rows, (const double*)r,
+                                        (const double*)old, (double*)out, om, k == 0, s);
+      } else if (L.D16) {
+        launch_bj_sweep<float, __nv_bfloat16>(ctx->np, ctx->dim, (const float*)Ainner(L), L.D16, L.nbr,
+                                              L.N, L.G, L.rows_pad, L.block_rows, (const float*)r,
+                                              (const float*)old, (float*)out, om, k == 0, s);
+      } else {
+        launch_bj_sweep<float, float>(ctx->np, ctx->dim, (const float*)Ainner(L), L.D32, L.nbr, L.N,
+                                      L.G, L.rows_pad, L.block_rows, (const float*)r,
+                                      (const float*)old, (float*)out, om, k == 0, s);
+      }
+    }
+    return buf[(sw - 1) & 1];
+  }
+
+  // z = BJ(r) from z = 0 on level lev (Alg. BJ); V is the level's vector type
+  template <typename V>
+  V* smooth(int lev, const V* r, cudaStream_t s) {
+    Level& L = ctx->lv[lev];
+    if (kMixed && lev == 0) {
+      launch_convert<double, float>((const double*)r, L.r_lo, L.N, s);
+      const float* out = (const float*)sweeps(L, (const T*)L.r_lo, (T*)L.z_lo, (T*)L.t_lo, s);
+      launch_convert<float, double>(out, (double*)L.z, L.N, s);
+      return static_cast<V*>(L.z);
+    }
+    return (V*)sweeps(L, (const T*)r, static_cast<T*>(L.z), static_cast<T*>(L.t), s);
+  }
+
+  // Alg. 1 on level lev with correction z (vectors in V, operator Aop)
+  template <typename V>
+  void rm(int lev, const V* Aop, const V* z, int end_iter, int htype, cudaStream_t s) {
+    Level& L = ctx->lv[lev];
+    V* W = static_cast<V*>(L.W);
+    V* Z = static_cast<V*>(L.Z);
+    V* w = static_cast<V*>(L.w);
+    V* wre = static_cast<V*>(L.wre);
+    EpiArgs none = epi(lev, EPI_NONE);
+    launch_spmv<V>(ctx->np, ctx->dim, Aop, L.nbr, L.N, L.G, L.rows_pad, L.block_rows, z, w,
+                   nullptr, L.partial, none, 0, s);
+    launch_gram_dots<V>(W, L.N, w, L.lcap, L.nblk, L.partial, epi(lev, EPI_GRAM1), 0, s);
+    launch_gram_apply<V>(W, L.N, w, wre, L.lcap, L.nblk, L.st, L.h, s);
+    launch_gram_dots<V>(W, L.N, wre, L.lcap, L.nblk, L.partial, epi(lev, EPI_GRAM2), 1, s);
+    launch_gram_update<V>(W, Z, L.N, w, wre, z, static_cast<V*>(L.r), L.lcap, L.nblk, L.partial,
+                          epi(lev, EPI_UPDATE), s);
+    EpiArgs fin = epi(lev, EPI_FINISH);
+    fin.end_iter = end_iter;
+    fin.hist_type = htype;
+    launch_rm_finish<V>(W, Z, L.N, static_cast<V*>(L.x), static_cast<V*>(L.r), L.nblk, L.partial,
+                        fin, s);
+  }
+
+  // one pass of the while body of Alg. 2 on level lev; V is the level's vector type
+  template <typename V>
+  void body(int lev, const V* Aop, cudaStream_t s) {
+    Level& L = ctx->lv[lev];
+    Level& C = ctx->lv[lev + 1];
+    V* z = smooth<V>(lev, static_cast<V*>(L.r), s);                       // pre-smoother
+    rm<V>(lev, Aop, z, 0, 1, s);
+    if (lev + 1 == ctx->nlev - 1) {                                        // direct solve
+      launch_restrict<T, V>(ctx->np, ctx->dim, L.n, C.n, Pm(), static_cast<V*>(L.r),
+                            static_cast<T*>(C.b), nullptr, nullptr, nullptr, EpiArgs{}, s);
+      launch_coarse_gemv<T>(ctx->Ainv, ctx->Nc, static_cast<T*>(C.b), static_cast<T*>(C.x), s);
+    } else {                                                               // recursion
+      if (capture) {
+        cudaGraph_t g;
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t* deps;
+        const cudaGraphEdgeData* ed;
+        size_t nd;
+        unsigned long long id;
+        CK(cudaStreamGetCaptureInfo(s, &cs, &id, &g, &deps, &ed, &nd));
+        CK(cudaGraphConditionalHandleCreate(&handle[lev + 1], g, 0, 0));
+      }
+      launch_restrict<T, V>(ctx->np, ctx->dim, L.n, C.n, Pm(), static_cast<V*>(L.r),
+                            static_cast<T*>(C.b), static_cast<T*>(C.r), static_cast<T*>(C.x),
+                            C.partial, epi(lev + 1, EPI_MG_BEGIN), s);
+      loop<T>(lev + 1, Ainner(C), s);
+    }
+    launch_prolong<T, V>(ctx->np, ctx->dim, L.n, C.n, Pm(), static_cast<T*>(C.x),
+                         static_cast<V*>(L.z), s);                         // z = P z_c
+    rm<V>(lev, Aop, static_cast<V*>(L.z), 0, 2, s);
+    z = smooth<V>(lev, static_cast<V*>(L.r), s);                           // post-smoother
+    rm<V>(lev, Aop, z, 1, 3, s);
+    // restart check: r = b - A x on request, then the loop condition of this level
+    launch_spmv<V>(ctx->np, ctx->dim, Aop, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
+                   static_cast<V*>(L.x), static_cast<V*>(L.r), static_cast<V*>(L.b), L.partial,
+                   epi(lev, EPI_RESTART), 1, s);
+  }
+
+  bool read_cond(int lev) {
+    int c = 0;
+    CK(cudaMemcpyAsync(&c, &ctx->lv[lev].st->cond, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    return c != 0;
+  }
+
+  // while (cond_lev) body(lev): host-driven, or a conditional while node when capturing
+  template <typename V>
+  void loop(int lev, const V* Aop, cudaStream_t s) {
+    if (!capture) {
+      while (read_cond(lev)) body<V>(lev, Aop, s);
+      return;
+    }
+    cudaGraph_t g;
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t* deps;
+    const cudaGraphEdgeData* ed;
+    size_t nd;
+    unsigned long long id;
+    CK(cudaStreamGetCaptureInfo(s, &cs, &id, &g, &deps, &ed, &nd));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle[lev];
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, deps, ed, nd, &cp));
+    CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaStream_t bs = ctx->cap[lev + 1];
+    CK(cudaStreamBeginCaptureToGraph(bs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeRelaxed));
+    body<V>(lev, Aop, bs);
+    CK(cudaStreamEndCapture(bs, nullptr));
+  }
+
+  // level 0: r0 = b - A x0 with the FP64 operator, then the level-0 loop
+  void run(cudaStream_t s) {
+    Level& L = ctx->lv[0];
+    if (capture) {
+      cudaGraph_t g;
+      cudaStreamCaptureStatus cs;
+      const cudaGraphNode_t* deps;
+      const cudaGraphEdgeData* ed;
+      size_t nd;
+      unsigned long long id;
+      CK(cudaStreamGetCaptureInfo(s, &cs, &id, &g, &deps, &ed, &nd));
+      CK(cudaGraphConditionalHandleCreate(&handle[0], g, 0, 0));
+    }
+    launch_spmv<T0>(ctx->np, ctx->dim, (const T0*)L.A64, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
+                    static_cast<T0*>(L.x), static_cast<T0*>(L.r), static_cast<T0*>(L.b), L.partial,
+                    epi(0, EPI_MG_BEGIN), 0, s);
+    loop<T0>(0, (const T0*)L.A64, s);
+  }
+};
+
+template <> const double* Cycle<double, double>::Ainner(const Level& L) const { return L.A64; }
+template <> const float* Cycle<double, float>::Ainner(const Level& L) const { return L.A32; }
+template <> const double* Cycle<double, double>::Pm() const { return ctx->P64; }
+template <> const float* Cycle<double, float>::Pm() const { return ctx->P32; }
+
+// host copy of the level states before a cycle
+void init_states(kcmg_ctx* ctx, double rtol0, double atol0, int maxit0) {
+  long long cap = (long long)maxit0 + 2;
+  for (int l = 0; l < ctx->nlev; ++l) {
+    if (l > 0) cap = cap * (ctx->p.lvl_maxit[l] > 0 ? ctx->p.lvl_maxit[l] : 1) + 2;
+    if (cap > (1LL << 30)) cap = 1LL << 30;
+    LevelState h;
+    memset(&h, 0, sizeof h);
+    h.level = l;
+    h.lcap = ctx->lv[l].lcap;
+    h.lmax = ctx->p.lmax;
+    h.maxit = (l == 0) ? maxit0 : ctx->p.lvl_maxit[l];
+    h.rtol = (l == 0) ? rtol0 : ctx->p.lvl_rtol[l];
+    h.atol = (l == 0) ? atol0 : 0.0;
+    h.status = KCMG_OK;
+    h.hist_cap = (l == 0) ? ctx->hist_cap : 0;
+    // breakdown threshold of Alg. 1 relative to ||A z||, by the level's precision
+    h.brk = (l == 0 || !ctx->mixed) ? 1e-14 : 1e-6;
+    h.guard = 0;
+    h.guard_cap = (int)cap;
+    if (!ctx->lv[l].st) continue;   // the coarsest level is solved directly: no state
+    CK(cudaMemcpyAsync(ctx->lv[l].st, &h, sizeof h, cudaMemcpyHostToDevice, ctx->s));
+  }
+  CK(cudaStreamSynchronize(ctx->s));
+}
+
+template <typename T>
+void run_cycle(kcmg_ctx* ctx) {
+  if (ctx->p.use_graph) {
+    if (!ctx->graph_ready) {
+      Cycle<double, T> cy{ctx};
+      cy.capture = true;
+      cudaGraph_t g;
+      CK(cudaStreamBeginCapture(ctx->s, cudaStreamCaptureModeRelaxed));
+      try {
+        cy.run(ctx->s);
+      } catch (...) {
+        cudaStreamEndCapture(ctx->s, &g);
+        cudaGetLastError();
+        throw;
+      }
+      CK(cudaStreamEndCapture(ctx->s, &g));
+      CK(cudaGraphInstantiate(&ctx->gexec, g, 0));
+      CK(cudaGraphDestroy(g));
+      ctx->graph_ready = true;
+    }
+    CK(cudaGraphLaunch(ctx->gexec, ctx->s));
+  } else {
+    Cycle<double, T> cy{ctx};
+    cy.run(ctx->s);
+  }
+  CK(cudaGetLastError());
+}
+
+// true FP64 residual r = b - A x with the FP64 operator; returns ||r||
+double fp64_residual(kcmg_ctx* ctx, const double* x, const double* b, double* r) {
+  Level& L = ctx->lv[0];
+  EpiArgs e;
+  e.st = L.st;  // only its reduction ticket is used
+  e.kind = EPI_NORM;
+  e.out = ctx->scal;
+  launch_spmv<double>(ctx->np, ctx->dim, L.A64, L.nbr, L.N, L.G, L.rows_pad, L.block_rows, x, r, b,
+                      L.partial, e, 0, ctx->s);
+  CK(cudaGetLastError());
+  double v = 0;
+  CK(cudaMemcpyAsync(&v, ctx->scal, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaStreamSynchronize(ctx->s));
+  return v;
+}
+
+struct StateReport {
+  LevelState st[KCMG_MAX_LEVELS];
+};
+
+void read_states(kcmg_ctx* ctx, StateReport& rep) {
+  memset(&rep, 0, sizeof rep);
+  for (int l = 0; l < ctx->nlev; ++l)
+    if (ctx->lv[l].st)
+      CK(cudaMemcpyAsync(&rep.st[l], ctx->lv[l].st, sizeof(LevelState), cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaStreamSynchronize(ctx->s));
+}
+
+void fill_info(kcmg_ctx* ctx, kcmg_info* info, const StateReport& rep, double res0, double rel) {
+  if (!info) return;
+  info->iters = rep.st[0].iters_total;
+  for (int l = 0; l < KCMG_MAX_LEVELS; ++l) info->level_iters[l] = l < ctx->nlev ? rep.st[l].iters_total : 0;
+  info->restarts = rep.st[0].nrestart;
+  // each level-0 restart replaces the recursive residual by the FP64 true residual:
+  // in the mixed form these are the refinement steps (plus the initial residual)
+  info->refinements = ctx->mixed ? rep.st[0].nrestart + 1 : 0;
+  info->res0 = res0;
+  info->rel_res = rel;
+  const int hl = rep.st[0].hist_len;
+  info->hist_len = 0;
+  if (info->hist && info->hist_type && info->hist_cap > 0) {
+    const int m = hl < info->hist_cap ? hl : info->hist_cap;
+    if (m > 0) {
+      CK(cudaMemcpyAsync(info->hist, ctx->hist, m * sizeof(double), cudaMemcpyDefault, ctx->s));
+      CK(cudaMemcpyAsync(info->hist_type, ctx->hist_type, m * sizeof(int), cudaMemcpyDefault, ctx->s));
+      CK(cudaStreamSynchronize(ctx->s));
+    }
+    info->hist_len = m;
+  }
+}
+
+kcmg_status solve_impl(kcmg_ctx* ctx, const double* b, double* x, double rtol, double atol,
+                       int maxiter, kcmg_info* info) {
+  Level& L = ctx->lv[0];
+  const size_t N = L.N;
+  StateReport rep;
+  copy_in(ctx, static_cast<double*>(L.b), b, N);
+  copy_in(ctx, static_cast<double*>(L.x), x, N);
+  init_states(ctx, rtol, atol, maxiter);
+  if (ctx->mixed) run_cycle<float>(ctx);
+  else run_cycle<double>(ctx);
+  read_states(ctx, rep);
+  const double rn = fp64_residual(ctx, static_cast<double*>(L.x), static_cast<double*>(L.b), ctx->ro);
+  const double r0 = rep.st[0].rnorm0;
+  copy_out(ctx, x, static_cast<double*>(L.x), N);
+  CK(cudaStreamSynchronize(ctx->s));
+  const double rel = r0 > 0 ? rn / r0 : 0.0;
+  fill_info(ctx, info, rep, r0, rel);
+  if (rep.st[0].status != KCMG_OK) return (kcmg_status)rep.st[0].status;
+  if (!std::isfinite(rn)) return KCMG_NONFINITE;
+  return (rn <= fmax(rtol * r0, atol)) ? KCMG_OK : KCMG_NOT_CONVERGED;
+}
+
+kcmg_ctx* build_ctx(const kcmg_params* p, cudaStream_t user, const double* blocks_override,
+                    kcmg_status* out_status, std::string* msg);
+
+}  // namespace
+
+// ====================================================================== C interface
+extern "C" {
+
+void kcmg_default_params(kcmg_params* p, int dim, int np, const int n[3], int nlevels) {
+  memset(p, 0, sizeof *p);
+  p->dim = dim;
+  p->np = np;
+  for (int j = 0; j < 3; ++j) p->n[j] = n ? n[j] : 1;
+  p->nlevels = nlevels;
+  p->omega = 0.7;
+  p->sweeps = 5;
+  for (int l = 0; l < KCMG_MAX_LEVELS; ++l) { p->lvl_rtol[l] = 0.0; p->lvl_maxit[l] = 1; }
+  p->lvl_rtol[1] = 0.1; p->lvl_maxit[1] = 20;
+  p->lvl_rtol[2] = 0.5; p->lvl_maxit[2] = 2;
+  p->lmax = 0;
+  p->precision = KCMG_FP64;
+  p->use_graph = 1;
+}
+
+const char* kcmg_status_string(kcmg_status s) {
+  switch (s) {
+    case KCMG_OK: return "ok";
+    case KCMG_NOT_CONVERGED: return "not converged";
+    case KCMG_BREAKDOWN: return "breakdown";
+    case KCMG_NONFINITE: return "non-finite value";
+    case KCMG_SINGULAR: return "singular block or coarse operator";
+    case KCMG_INVALID_ARG: return "invalid argument";
+    case KCMG_OOM: return "out of device memory";
+    case KCMG_CUDA_ERROR: return "CUDA error";
+  }
+  return "unknown";
+}
+
+const char* kcmg_last_error(const kcmg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int kcmg_level_cells(const kcmg_ctx* ctx, int level) {
+  if (!ctx || level < 0 || level >= ctx->nlev) return 0;
+  return ctx->lv[level].ncell;
+}
+
+void kcmg_destroy(kcmg_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->adj && ctx->adj != ctx) kcmg_destroy(ctx->adj);
+  if (ctx->s) cudaStreamSynchronize(ctx->s);
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  for (void* p : ctx->allocs) cudaFree(p);
+  if (ctx->stage_big) cudaFree(ctx->stage_big);
+  for (auto& c : ctx->cap) if (c) cudaStreamDestroy(c);
+  if (ctx->s) cudaStreamDestroy(ctx->s);
+  if (ctx->ev) cudaEventDestroy(ctx->ev);
+  delete ctx;
+}
+
+kcmg_status kcmg_setup(kcmg_ctx** out, const kcmg_params* p, void* cuda_stream) {
+  if (!out || !p) return KCMG_INVALID_ARG;
+  *out = nullptr;
+  kcmg_status st = KCMG_OK;
+  std::string msg;
+  kcmg_ctx* ctx = build_ctx(p, (cudaStream_t)cuda_stream, nullptr, &st, &msg);
+  *out = ctx;
+  return st;
+}
+
+}  // extern "C"
+
+namespace {
+
+kcmg_ctx* build_ctx(const kcmg_params* p, cudaStream_t user, const double* blocks_override,
+                    kcmg_status* out_status, std::string* msg) {
+  kcmg_ctx* ctx = new kcmg_ctx();
+  ctx->p = *p;
+  try {
+    REQUIRE(p->dim == 2 || p->dim == 3, "dim must be 2 or 3");
+    REQUIRE(np_supported(p->np), "unsupported np %d (3, 4, 6, 10, 20)", p->np);
+    REQUIRE(p->nlevels >= 2 && p->nlevels <= KCMG_MAX_LEVELS, "nlevels must be in [2, %d]", KCMG_MAX_LEVELS);
+    REQUIRE(p->blocks && p->prolong, "blocks and prolong must be set");
+    REQUIRE(p->sweeps >= 1 && p->sweeps <= 64, "sweeps must be in [1, 64]");
+    REQUIRE(p->precision >= 0 && p->precision <= 2, "unknown precision %d", p->precision);
+    for (int j = 0; j < p->dim; ++j)
+      REQUIRE(p->n[j] > 0 && p->n[j] % (1 << (p->nlevels - 1)) == 0,
+              "n[%d] = %d is not divisible by 2^(nlevels-1)", j, p->n[j]);
+    REQUIRE(p->lmax >= 0 && p->lmax <= kLcapMax - 3, "lmax must be in [0, %d]", kLcapMax - 3);
+    ctx->dim = p->dim;
+    ctx->np = p->np;
+    ctx->S = 2 * p->dim + 1;
+    ctx->nlev = p->nlevels;
+    ctx->nch = 1 << p->dim;
+    ctx->mixed = p->precision != KCMG_FP64;
+    ctx->user = user;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaStreamCreateWithFlags(&ctx->s, cudaStreamNonBlocking));
+    for (int l = 0; l < KCMG_MAX_LEVELS + 2; ++l) CK(cudaStreamCreateWithFlags(&ctx->cap[l], cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&ctx->ev, cudaEventDisableTiming));
+    if (user) {
+      CK(cudaEventRecord(ctx->ev, user));
+      CK(cudaStreamWaitEvent(ctx->s, ctx->ev, 0));
+    }
+    ctx->lv.resize(ctx->nlev);
+    ctx->dflag = dalloc<int>(ctx, 4);
+    ctx->scal = dalloc<double>(ctx, 8);
+    const size_t bs = (size_t)ctx->np * ctx->np;
+    ctx->P64 = dalloc<double>(ctx, ctx->nch * bs);
+    copy_in(ctx, ctx->P64, p->prolong, ctx->nch * bs);
+    ctx->P32 = dalloc<float>(ctx, ctx->nch * bs);
+    launch_convert<double, float>(ctx->P64, ctx->P32, ctx->nch * bs, ctx->s);
+    build_hierarchy(ctx, blocks_override ? blocks_override : p->blocks);
+    // cycle vectors: level 0 basis capacity from lmax (or a default), coarse levels from
+    // the per-level iteration caps (3 stored corrections per cycle)
+    for (int l = 0; l < ctx->nlev - 1; ++l) {
+      int cap;
+      if (l == 0) cap = p->lmax > 0 ? p->lmax + 3 : 512;
+      else cap = 3 * (p->lvl_maxit[l] > 0 ? p->lvl_maxit[l] : 1) + 3;
+      if (p->lmax > 0 && l > 0 && p->lmax + 3 < cap) cap = p->lmax + 3;
+      if (cap > kLcapMax) cap = kLcapMax;
+      // keep the level-0 basis within a third of the free device memory
+      if (l == 0) {
+        size_t fr = 0, tot = 0;
+        CK(cudaMemGetInfo(&fr, &tot));
+        const size_t per = (size_t)2 * ctx->lv[0].N * sizeof(double);
+        while (cap > 16 && (size_t)cap * per > fr / 3) cap /= 2;
+      }
+      // level 0 is FP64 in both forms; the mixed form runs every other level in FP32
+      if (ctx->mixed && l > 0) alloc_cycle_vectors<float>(ctx, ctx->lv[l], cap);
+      else alloc_cycle_vectors<double>(ctx, ctx->lv[l], cap);
+      if (ctx->mixed && l == 0) {
+        Level& L0 = ctx->lv[0];
+        L0.r_lo = dalloc<float>(ctx, L0.N);
+        L0.z_lo = dalloc<float>(ctx, L0.N);
+        L0.t_lo = dalloc<float>(ctx, L0.N);
+      }
+    }
+    {  // coarsest level: b (restricted residual) and x (direct solution) only
+      Level& C = ctx->lv[ctx->nlev - 1];
+      const size_t es = ctx->mixed ? sizeof(float) : sizeof(double);
+      C.b = dalloc<unsigned char>(ctx, C.N * es);
+      C.x = dalloc<unsigned char>(ctx, C.N * es);
+    }
+    const size_t N0 = ctx->lv[0].N;
+    ctx->ro = dalloc<double>(ctx, N0);
+    ctx->hist = dalloc<double>(ctx, ctx->hist_cap);
+    ctx->hist_type = dalloc<int>(ctx, ctx->hist_cap);
+    size_t maxN = 0;
+    for (auto& L : ctx->lv) maxN = maxN > (size_t)L.N ? maxN : (size_t)L.N;
+    ctx->stage_in = dalloc<double>(ctx, maxN);
+    ctx->stage_out = dalloc<double>(ctx, maxN);
+    CK(cudaStreamSynchronize(ctx->s));
+    *out_status = KCMG_OK;
+    return ctx;
+  } catch (Fail& f) {
+    *out_status = f.st;
+    if (msg) *msg = ctx->err;
+    // keep the context so that kcmg_last_error can report; the caller destroys it
+    return ctx;
+  }
+}
+
+// vectors of a level are FP64 on level 0 and in both forms' FP64 levels, FP32 otherwise
+bool level_is_f32(const kcmg_ctx* ctx, int lev) { return ctx->mixed && lev > 0; }
+
+// FP64 user vector -> level buffer of the level's type
+void load_vec(kcmg_ctx* ctx, int lev, void* dst, const double* src, size_t n) {
+  copy_in(ctx, ctx->stage_in, src, n);
+  if (level_is_f32(ctx, lev)) launch_convert<double, float>(ctx->stage_in, static_cast<float*>(dst), n, ctx->s);
+  else CK(cudaMemcpyAsync(dst, ctx->stage_in, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->s));
+}
+void store_vec(kcmg_ctx* ctx, int lev, double* dst, const void* src, size_t n) {
+  if (level_is_f32(ctx, lev)) launch_convert<float, double>(static_cast<const float*>(src), ctx->stage_out, n, ctx->s);
+  else CK(cudaMemcpyAsync(ctx->stage_out, src, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->s));
+  copy_out(ctx, dst, ctx->stage_out, n);
+  CK(cudaStreamSynchronize(ctx->s));
+}
+
+template <typename F>
+kcmg_status guarded(kcmg_ctx* ctx, F&& f) {
+  if (!ctx) return KCMG_INVALID_ARG;
+  try {
+    if (ctx->user) {
+      CK(cudaEventRecord(ctx->ev, ctx->user));
+      CK(cudaStreamWaitEvent(ctx->s, ctx->ev, 0));
+    }
+    kcmg_status st = f();
+    if (ctx->user) {
+      CK(cudaEventRecord(ctx->ev, ctx->s));
+      CK(cudaStreamWaitEvent(ctx->user, ctx->ev, 0));
+    }
+    return st;
+  } catch (Fail& e) {
+    return e.st;
+  }
+}
+
+kcmg_status ensure_adjoint(kcmg_ctx* ctx) {
+  if (ctx->adj_built) return KCMG_OK;
+  Level& F = ctx->lv[0];
+  const size_t tot = (size_t)ctx->S * F.ncell * ctx->np * ctx->np;
+  double* tr = nullptr;
+  CK(cudaMalloc(&tr, tot * sizeof(double)));
+  launch_transpose_blocks(ctx->np, ctx->dim, F.nat, F.nbr, F.ncell, tr, ctx->s);
+  unsigned int* cnt = reinterpret_cast<unsigned int*>(ctx->dflag);
+  CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned int), ctx->s));
+  launch_count_diff(F.nat, tr, tot, cnt, ctx->s);
+  unsigned int nd = 0;
+  CK(cudaMemcpyAsync(&nd, cnt, sizeof nd, cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaStreamSynchronize(ctx->s));
+  if (nd == 0) {
+    ctx->adj = ctx;
+  } else {
+    kcmg_status st = KCMG_OK;
+    std::string msg;
+    kcmg_params pa = ctx->p;
+    pa.prolong = ctx->P64;   // the caller's setup arrays may be gone by now
+    pa.blocks = tr;
+    kcmg_ctx* a = build_ctx(&pa, nullptr, tr, &st, &msg);
+    if (st != KCMG_OK) {
+      set_err(ctx, "adjoint setup failed: %s", msg.c_str());
+      kcmg_destroy(a);
+      cudaFree(tr);
+      return st;
+    }
+    ctx->adj = a;
+  }
+  cudaFree(tr);
+  ctx->adj_built = true;
+  return KCMG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+kcmg_status kcmg_solve(kcmg_ctx* ctx, const double* b, double* x, int nrhs, double rtol,
+                       double atol, int maxiter, kcmg_info* info) {
+  return guarded(ctx, [&]() -> kcmg_status {
+    REQUIRE(b && x, "b and x must be non-null");
+    REQUIRE(nrhs == 1, "nrhs must be 1");
+    REQUIRE(rtol >= 0 && atol >= 0 && maxiter >= 0, "negative tolerance or maxiter");
+    return solve_impl(ctx, b, x, rtol, atol, maxiter, info);
+  });
+}
+
+kcmg_status kcmg_solve_adjoint(kcmg_ctx* ctx, const double* g, double* lambda, int nrhs,
+                               double rtol, double atol, int maxiter, kcmg_info* info) {
+  return guarded(ctx, [&]() -> kcmg_status {
+    REQUIRE(g && lambda, "g and lambda must be non-null");
+    REQUIRE(nrhs == 1, "nrhs must be 1");
+    kcmg_status st = ensure_adjoint(ctx);
+    if (st != KCMG_OK) return st;
+    if (ctx->adj == ctx) return solve_impl(ctx, g, lambda, rtol, atol, maxiter, info);
+    kcmg_status s2 = solve_impl(ctx->adj, g, lambda, rtol, atol, maxiter, info);
+    if (s2 != KCMG_OK && s2 != KCMG_NOT_CONVERGED) set_err(ctx, "%s", ctx->adj->err.c_str());
+    return s2;
+  });
+}
+
+kcmg_status kcmg_apply(kcmg_ctx* ctx, int level, int op, const double* x, double* y) {
+  return guarded(ctx, [&]() -> kcmg_status {
+    REQUIRE(level >= 0 && level < ctx->nlev && x && y, "bad level or null vector");
+    REQUIRE(op == 0 || (op == 1 && ctx->mixed), "op 1 needs a mixed-precision context");
+    Level& L = ctx->lv[level];
+    copy_in(ctx, ctx->stage_in, x, L.N);
+    EpiArgs none;
+    if (op == 0) {
+      launch_spmv<double>(ctx->np, ctx->dim, L.A64, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
+                          ctx->stage_in, ctx->stage_out, nullptr, nullptr, none, 0, ctx->s);
+    } else {
+      float* xi = ctx->lv[0].r_lo;    // FP32 scratch of the finest size
+      float* yi = ctx->lv[0].z_lo;
+      launch_convert<double, float>(ctx->stage_in, xi, L.N, ctx->s);
+      launch_spmv<float>(ctx->np, ctx->dim, L.A32, L.nbr, L.N, L.G, L.rows_pad, L.block_rows, xi,
+                         yi, nullptr, nullptr, none, 0, ctx->s);
+      launch_convert<float, double>(yi, ctx->stage_out, L.N, ctx->s);
+    }
+    CK(cudaGetLastError());
+    copy_out(ctx, y, ctx->stage_out, L.N);
+    CK(cudaStreamSynchronize(ctx->s));
+    return KCMG_OK;
+  });
+}
+
+kcmg_status kcmg_smooth(kcmg_ctx* ctx, int level, const double* r, double* z) {
+  return guarded(ctx, [&]() -> kcmg_status {
+    REQUIRE(level >= 0 && level < ctx->nlev - 1 && r && z, "bad level or null vector");
+    Level& L = ctx->lv[level];
+    load_vec(ctx, level, L.b, r, L.N);
+    const void* out;
+    if (ctx->mixed) {
+      Cycle<double, float> cy{ctx};
+      if (level == 0) out = cy.smooth<double>(0, static_cast<double*>(L.b), ctx->s);
+      else out = cy.smooth<float>(level, static_cast<float*>(L.b), ctx->s);
+    } else {
+      Cycle<double, double> cy{ctx};
+      out = cy.smooth<double>(level, static_cast<double*>(L.b), ctx->s);
+    }
+    CK(cudaGetLastError());
+    store_vec(ctx, level, z, out, L.N);
+    return KCMG_OK;
+  });
+}
+
+kcmg_status kcmg_restrict(kcmg_ctx* ctx, int level, const double* r, double* rc) {
+  return guarded(ctx, [&]() -> kcmg_status {
+    REQUIRE(level >= 0 && level < ctx->nlev - 1 && r && rc, "bad level or null vector");
+    Level &L = ctx->lv[level], &C = ctx->lv[level + 1];
+    load_vec(ctx, level, L.t, r, L.N);
+    if (!ctx->mixed)
+      launch_restrict<double, double>(ctx->np, ctx->dim, L.n, C.n, ctx->P64, static_cast<double*>(L.t),
+                                      static_cast<double*>(C.b), nullptr, nullptr, nullptr, EpiArgs{}, ctx->s);
+    else if (level == 0)
+      launch_restrict<float, double>(ctx->np, ctx->dim, L.n, C.n, ctx->P32, static_cast<double*>(L.t),
+                                     static_cast<float*>(C.b), nullptr, nullptr, nullptr, EpiArgs{}, ctx->s);
+    else
+      launch_restrict<float, float>(ctx->np, ctx->dim, L.n, C.n, ctx->P32, static_cast<float*>(L.t),
+                                    static_cast<float*>(C.b), nullptr, nullptr, nullptr, EpiArgs{}, ctx->s);
+    CK(cudaGetLastError());
+    store_vec(ctx, level + 1, rc, C.b, C.N);
+    return KCMG_OK;
+  });
+}
+
+kcmg_status kcmg_prolong(kcmg_ctx* ctx, int level, const double* zc, double* z) {
+  return guarded(ctx, [&]() -> kcmg_status {
+    REQUIRE(level >= 0 && level < ctx->nlev - 1 && zc && z, "bad level or null vector");
+    Level &L = ctx->lv[level], &C = ctx->lv[level + 1];
+    load_vec(ctx, level + 1, C.x, zc, C.N);
+    if (!ctx->mixed)
+      launch_prolong<double, double>(ctx->np, ctx->dim, L.n, C.n, ctx->P64, static_cast<double*>(C.x),
+                                     static_cast<double*>(L.t), ctx->s);
+    else if (level == 0)
+      launch_prolong<float, double>(ctx->np, ctx->dim, L.n, C.n, ctx->P32, static_cast<float*>(C.x),
+                                    static_cast<double*>(L.t), ctx->s);
+    else
+      launch_prolong<float, float>(ctx->np, ctx->dim, L.n, C.n, ctx->P32, static_cast<float*>(C.x),
+                                   static_cast<float*>(L.t), ctx->s);
+    CK(cudaGetLastError());
+    store_vec(ctx, level, z, L.t, L.N);
+    return KCMG_OK;
+  });
+}
+
+kcmg_status kcmg_coarse_solve(kcmg_ctx* ctx, const double* r, double* z) {
+  return guarded(ctx, [&]() -> kcmg_status {
+    REQUIRE(r && z, "null vector");
+    copy_in(ctx, ctx->stage_in, r, ctx->Nc);
+    launch_coarse_gemv<double>(ctx->Ainv, ctx->Nc, ctx->stage_in, ctx->stage_out, ctx->s);
+    CK(cudaGetLastError());
+    copy_out(ctx, z, ctx->stage_out, ctx->Nc);
+    CK(cudaStreamSynchronize(ctx->s));
+    return KCMG_OK;
+  });
+}
+
+kcmg_status kcmg_get_blocks(kcmg_ctx* ctx, int level, double* out) {
+  return guarded(ctx, [&]() -> kcmg_status {
+    REQUIRE(level >= 0 && level < ctx->nlev && out, "bad level or null output");
+    Level& L = ctx->lv[level];
+    copy_out(ctx, out, L.nat, (size_t)ctx->S * L.ncell * ctx->np * ctx->np);
+    CK(cudaStreamSynchronize(ctx->s));
+    return KCMG_OK;
+  });
+}
+
+}  // extern "C"
+
+namespace {
+template <typename T0, typename T, typename V>
+void rm_sequence_impl(kcmg_ctx* ctx, int level, const double* z, int ncorr) {
+  Level& L = ctx->lv[level];
+  Cycle<T0, T> cy{ctx};
+  const V* Aop = (level == 0) ? (const V*)L.A64 : (const V*)cy.Ainner(L);
+  launch_spmv<V>(ctx->np, ctx->dim, Aop, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
+                 static_cast<V*>(L.x), static_cast<V*>(L.r), static_cast<V*>(L.b), L.partial,
+                 cy.epi(level, EPI_MG_BEGIN), 0, ctx->s);
+  for (int k = 0; k < ncorr; ++k) {
+    load_vec(ctx, level, L.z, z + (size_t)k * L.N, L.N);
+    cy.template rm<V>(level, Aop, static_cast<V*>(L.z), 0, 1, ctx->s);
+  }
+}
+}  // namespace
+
+extern "C" {
+
+kcmg_status kcmg_rm_sequence(kcmg_ctx* ctx, int level, const double* b, const double* x0,
+                             const double* z, int ncorr, double* x, double* r, int* l) {
+  return guarded(ctx, [&]() -> kcmg_status {
+    REQUIRE(level >= 0 && level < ctx->nlev - 1 && b && x0 && x && r && l && (ncorr == 0 || z),
+            "bad arguments");
+    Level& L = ctx->lv[level];
+    REQUIRE(ncorr <= L.lcap, "ncorr %d exceeds the basis capacity %d", ncorr, L.lcap);
+    init_states(ctx, 0.0, 0.0, 1 << 30);
+    load_vec(ctx, level, L.b, b, L.N);
+    load_vec(ctx, level, L.x, x0, L.N);
+    if (!ctx->mixed) rm_sequence_impl<double, double, double>(ctx, level, z, ncorr);
+    else if (level == 0) rm_sequence_impl<double, float, double>(ctx, level, z, ncorr);
+    else rm_sequence_impl<double, float, float>(ctx, level, z, ncorr);
+    CK(cudaGetLastError());
+    store_vec(ctx, level, x, L.x, L.N);
+    store_vec(ctx, level, r, L.r, L.N);
+    LevelState h;
+    CK(cudaMemcpyAsync(&h, L.st, sizeof h, cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    *l = h.l;
+    return KCMG_OK;
+  });
+}
+
+kcmg_status kcmg_grad_lognu(kcmg_ctx* ctx, const double* nu, const double* V, const double* F,
+                            const double* B, const double* lambda, const double* u, double* g) {
+  return guarded(ctx, [&]() -> kcmg_status {
+    REQUIRE(nu && V && F && B && lambda && u && g, "null argument");
+    Level& L = ctx->lv[0];
+    const size_t bs = (size_t)ctx->np * ctx->np;
+    const size_t need = L.ncell + bs + 4 * ctx->dim * bs + 2 * ctx->dim * bs + 2 * (size_t)L.N + L.ncell;
+    if (ctx->stage_big_len < need) {
+      if (ctx->stage_big) cudaFree(ctx->stage_big);
+      ctx->stage_big = nullptr;
+      CK(cudaMalloc(&ctx->stage_big, need * sizeof(double)));
+      ctx->stage_big_len = need;
+    }
+    double* p = ctx->stage_big;
+    double *dnu = p, *dV = dnu + L.ncell, *dF = dV + bs, *dB = dF + 4 * ctx->dim * bs,
+           *dl = dB + 2 * ctx->dim * bs, *du = dl + L.N, *dg = du + L.N;
+    copy_in(ctx, dnu, nu, L.ncell);
+    copy_in(ctx, dV, V, bs);
+    copy_in(ctx, dF, F, 4 * ctx->dim * bs);
+    copy_in(ctx, dB, B, 2 * ctx->dim * bs);
+    copy_in(ctx, dl, lambda, L.N);
+    copy_in(ctx, du, u, L.N);
+    launch_grad_lognu(ctx->np, ctx->dim, L.n, dnu, dV, dF, dB, dl, du, dg, ctx->s);
+    CK(cudaGetLastError());
+    copy_out(ctx, g, dg, L.ncell);
+    CK(cudaStreamSynchronize(ctx->s));
+    return KCMG_OK;
+  });
+}
+
+}  // extern "C"

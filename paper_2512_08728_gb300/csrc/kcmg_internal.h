@@ -1,0 +1,144 @@
+// Internal declarations shared by the kernel and engine translation units of libkcmg.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "kcmg.h"
+
+namespace kcmg {
+
+// Fixed launch shapes.  Grid sizes of reductions depend only on the vector length, so
+// every reduction tree (and therefore every result) is bitwise reproducible.
+constexpr int kVecThreads = 256;   // element-wise / dot kernels
+constexpr int kDotBlocksMax = 304; // 2 blocks per SM on a 152-SM GB300
+constexpr int kMaxNp = 20;
+constexpr int kLcapMax = 2048;     // basis capacity cap per level (shared-memory sizing)
+constexpr int kMaxChild = 8;
+
+// flags of the RM call in flight
+enum : int { F_REORTH = 1, F_DISCARD = 2 };
+
+// Device-resident scalar state of one level of the cycle.  One MG call is active per
+// level at any time (Alg. 2 recursion), so one state per level suffices.
+struct LevelState {
+  int level;
+  int l;            // stored basis vectors (columns of W, Z)
+  int lcap;         // device capacity of W, Z
+  int lmax;         // user restart length (0 = capacity)
+  int it, maxit;    // cycles of the current MG call and the cap
+  int iters_total;  // cycles summed over visits
+  int flags;        // F_REORTH / F_DISCARD of the RM call in flight
+  int breakdowns;   // consecutive discarded corrections (level 0)
+  int status;       // kcmg_status (level 0)
+  int cond;         // loop condition of the while node
+  int restart_req;  // restart at the end of this cycle
+  int nrestart;
+  int hist_len, hist_cap;
+  int guard, guard_cap; // loop bodies executed on this level in this solve, and their cap
+  unsigned int ticket;  // last-block counter of the reduction kernels
+  double rnorm, rnorm0, eps, rtol, atol;
+  double naz2;      // ||A z||^2 of the RM call in flight
+  double gamma, alpha;
+  double brk;       // breakdown threshold relative to ||A z||
+};
+
+enum EpiKind : int {
+  EPI_NONE = 0,
+  EPI_MG_BEGIN,     // sum = ||r0||^2: start of an MG call on the level
+  EPI_GRAM1,        // sums = W^T w, ||w||^2
+  EPI_GRAM2,        // sums = W^T w' (reorthogonalisation pass)
+  EPI_UPDATE,       // sums = ||w_hat||^2, w_hat . r
+  EPI_FINISH,       // sum = ||r||^2 after the x, r update
+  EPI_RESTART,      // sum = ||b - A x||^2: restart of the level
+  EPI_NORM          // sum = ||y||^2 stored into *out (component calls, refinement)
+};
+
+struct EpiArgs {
+  LevelState* st = nullptr;
+  int kind = EPI_NONE;
+  int end_iter = 0;      // EPI_FINISH: last RM of the cycle
+  int hist_type = 0;     // EPI_FINISH: 1 pre, 2 coarse, 3 post
+  int use_handle = 0;
+  cudaGraphConditionalHandle handle = 0;
+  double* h = nullptr;   // Gram coefficients, pass 1 [lcap]
+  double* h2 = nullptr;  // Gram coefficients, pass 2 [lcap]
+  double* hist = nullptr;
+  int* hist_type_buf = nullptr;
+  double* out = nullptr; // EPI_NORM destination
+};
+
+// ---------------------------------------------------------------- kernel launchers
+// All take the stream last; T = double or float (storage and arithmetic type).
+// Operator layout ("row-interleaved"): element (s, row, j) of slot s, DOF row
+// row = cell*np + i, column j sits at ((s*G + row/32)*JP + j/2)*64 + (row%32)*2 + j%2,
+// G = padded rows / 32, JP = ceil(np/2); padded rows and odd-np padding are zero.
+
+template <typename T>
+void launch_spmv(int np, int dim, const T* A, const int* nbr, int N, int G, int rows_pad,
+                 int block_rows, const T* x, T* y, const T* b, double* partial,
+                 const EpiArgs& e, int conditional, cudaStream_t s);
+template <typename T, typename TI>
+void launch_bj_sweep(int np, int dim, const T* A, const TI* Dinv, const int* nbr, int N, int G,
+                     int rows_pad, int block_rows, const T* r, const T* zold, T* znew,
+                     double omega, int first, cudaStream_t s);
+// restriction reads the fine residual in TIN (FP64 at level 0 of the mixed form),
+// prolongation writes the fine correction in TOUT
+template <typename T, typename TIN>
+void launch_restrict(int np, int dim, const int* nf, const int* nc, const T* P, const TIN* rf,
+                     T* b, T* r, T* x, double* partial, const EpiArgs& e, cudaStream_t s);
+template <typename T, typename TOUT>
+void launch_prolong(int np, int dim, const int* nf, const int* nc, const T* P, const T* zc,
+                    TOUT* zf, cudaStream_t s);
+template <typename T>
+void launch_coarse_gemv(const double* Ainv, int n, const T* b, T* x, cudaStream_t s);
+template <typename T>
+void launch_gram_dots(const T* W, int N, const T* w, int lcap, int nblk, double* partial,
+                      const EpiArgs& e, int conditional, cudaStream_t s);
+template <typename T>
+void launch_gram_apply(const T* W, int N, const T* w, T* wout, int lcap, int nblk,
+                       LevelState* st, const double* h, cudaStream_t s);
+template <typename T>
+void launch_gram_update(const T* W, const T* Z, int N, const T* w, const T* wre, const T* z,
+                        const T* r, int lcap, int nblk, double* partial, const EpiArgs& e,
+                        cudaStream_t s);
+template <typename T>
+void launch_rm_finish(T* W, T* Z, int N, T* x, T* r, int nblk, double* partial,
+                      const EpiArgs& e, cudaStream_t s);
+template <typename T>
+void launch_norm(const T* v, int N, int nblk, double* partial, const EpiArgs& e,
+                 cudaStream_t s);
+void launch_control(const EpiArgs& e, cudaStream_t s);  // cond from the current state
+
+// conversions and vector utilities
+template <typename Ts, typename Td>
+void launch_convert(const Ts* src, Td* dst, size_t n, cudaStream_t s);
+template <typename T>
+void launch_axpy_to_double(const T* e, double* x, size_t n, cudaStream_t s); // x += e
+
+// setup kernels (FP64, natural layout [S][C][np][np])
+int launch_galerkin(int np, int dim, const double* Af, const int* nbrf, const int* nf,
+                    const int* nc, const double* P, double* Ac, cudaStream_t s);
+int launch_block_inverse(int np, const double* diag, int ncell, double* inv, int* fail,
+                         cudaStream_t s);
+void launch_dense_gj_step(double* M, int n, int c, double* fcol, int* fail, cudaStream_t s);
+void launch_assemble_dense(int np, int dim, const double* blk, const int* nbr, int ncell,
+                           double* M /*[n][2n]*/, cudaStream_t s);
+void launch_extract_inverse(const double* M, int n, double* Ainv, cudaStream_t s);
+template <typename T>
+void launch_interleave(int np, int nslot, const double* nat, int ncell, int G, T* out,
+                       cudaStream_t s);
+void launch_transpose_blocks(int np, int dim, const double* in, const int* nbr, int ncell,
+                             double* out, cudaStream_t s);
+void launch_count_diff(const double* a, const double* b, size_t n, unsigned int* cnt,
+                       cudaStream_t s);
+void launch_build_nbr(int dim, const int* n, int* nbr, cudaStream_t s);
+void launch_grad_lognu(int np, int dim, const int* n, const double* nu, const double* V,
+                       const double* F, const double* B, const double* lam, const double* u,
+                       double* g, cudaStream_t s);
+
+int block_rows_for(int np);  // threads per block of the operator kernels (whole cells)
+bool np_supported(int np);
+
+}  // namespace kcmg

@@ -1,0 +1,246 @@
+"""Parity of the CUDA path (through the C interface) with the CPU oracle.
+
+Tolerances: FP64 kernels agree with the oracle to rounding (1e-12 relative to the largest
+entry); FP32 kernels to 1e-5; whole solves reach a true FP64 relative residual <= 1e-10
+and a solution within 1e-8 (relative, 2-norm) of the oracle's solution.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2512_08728_gb300 as pkg
+from oracle import OracleSolver, grad_lognu
+from workloads import dense_matrix, make_problem, workload
+
+pytestmark = pytest.mark.gpu
+
+SMALL = ["sipg2d_p1_16x16", "sipg3d_p1_8x4x4", "sipg2d_p2_32x16", "sipg3d_p2_8cube",
+         "sipg3d_p3_8cube_zstretch"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pkg.build()
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _problem(name, seed=0):
+    if name == "ragged_3d_p2":
+        return make_problem(3, 2, (6, 6, 2), 2, seed=seed)
+    return workload(name).make(seed)
+
+
+@pytest.mark.parametrize("name", SMALL + ["ragged_3d_p2"])
+def test_operator_galerkin_and_transfers(name):
+    pr = _problem(name)
+    orc = OracleSolver.from_problem(pr)
+    s = pkg.KCycleSolver(pr, precision="mixed")
+    rng = np.random.default_rng(1)
+    for lev in range(pr.nlevels):
+        assert _rel(s.blocks(lev), orc.blocks(lev)) < 1e-13
+        x = rng.standard_normal(orc.ndof(lev))
+        y = orc.apply(lev, x)
+        assert _rel(s.apply(lev, x, op=0), y) < 1e-13
+        assert _rel(s.apply(lev, x, op=1), y) < 2e-6
+        if lev + 1 < pr.nlevels:
+            r = rng.standard_normal(orc.ndof(lev))
+            zc = rng.standard_normal(orc.ndof(lev + 1))
+            assert _rel(s.restrict(lev, r), orc.restrict(lev, r)) < 1e-5
+            assert _rel(s.prolong(lev, zc), orc.prolong(lev, zc)) < 1e-5
+    s.close()
+
+
+@pytest.mark.parametrize("name", SMALL + ["ragged_3d_p2"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 3e-5), ("mixed_bf16", 2e-2)])
+def test_block_jacobi_smoother(name, precision, tol):
+    pr = _problem(name)
+    orc = OracleSolver.from_problem(pr)
+    s = pkg.KCycleSolver(pr, precision=precision)
+    rng = np.random.default_rng(2)
+    for lev in range(pr.nlevels - 1):
+        r = rng.standard_normal(orc.ndof(lev))
+        assert _rel(s.smooth(lev, r), orc.smooth(lev, r)) < tol
+    s.close()
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_fp64_transfers_and_coarse_solve(name):
+    pr = _problem(name)
+    orc = OracleSolver.from_problem(pr)
+    s = pkg.KCycleSolver(pr, precision="fp64")
+    rng = np.random.default_rng(3)
+    for lev in range(pr.nlevels - 1):
+        r = rng.standard_normal(orc.ndof(lev))
+        zc = rng.standard_normal(orc.ndof(lev + 1))
+        assert _rel(s.restrict(lev, r), orc.restrict(lev, r)) < 1e-13
+        assert _rel(s.prolong(lev, zc), orc.prolong(lev, zc)) < 1e-13
+    rc = rng.standard_normal(orc.ndof(pr.nlevels - 1))
+    assert _rel(s.coarse_solve(rc), orc.coarse_solve(rc)) < 1e-9
+    s.close()
+
+
+@pytest.mark.parametrize("name", ["sipg2d_p1_16x16", "sipg3d_p2_8cube", "ragged_3d_p2"])
+def test_residual_minimization_sequence(name):
+    """Alg. 1 on the GPU (classical Gram-Schmidt with a reorthogonalisation test) against
+    the oracle's modified Gram-Schmidt, on the same corrections: smoother outputs, coarse
+    corrections and random vectors, including a linearly dependent one (discarded)."""
+    pr = _problem(name)
+    orc = OracleSolver.from_problem(pr)
+    s = pkg.KCycleSolver(pr, precision="fp64")
+    rng = np.random.default_rng(4)
+    x0 = rng.uniform(-1, 1, pr.ndof)
+    orc.rm_begin(0, pr.b, x0)
+    r = pr.b - orc.apply(0, x0)
+    zs = []
+    for k in range(24):
+        kind = k % 4
+        if kind == 0:
+            z = orc.smooth(0, r)
+        elif kind == 1:
+            z = orc.prolong(0, orc.restrict(0, r))
+        elif kind == 2:
+            z = rng.uniform(-1, 1, pr.ndof)
+        else:
+            z = 2.0 * zs[-1]                  # dependent: must be discarded
+        zs.append(z)
+        rc, xo, r, lo = orc.rm_call(0, z)
+    xg, rg, lg = s.rm_sequence(0, pr.b, x0, np.stack(zs))
+    assert lg == lo
+    # rounding of the two recursions (incremental on the GPU, from scratch in the oracle)
+    # scales with the initial residual b - A x0, which a random x0 makes large
+    scale = np.linalg.norm(pr.b - orc.apply(0, x0))
+    assert np.linalg.norm(rg - r) <= 1e-10 * scale
+    assert np.linalg.norm(xg - xo) <= 1e-7 * np.linalg.norm(xo)
+    s.close()
+
+
+def _check_solution(pr, x, info, x_or, tol_err=1e-8):
+    # true residual evaluated by the oracle's operator, independent of the GPU
+    orc = OracleSolver.from_problem(pr)
+    rel = np.linalg.norm(pr.b - orc.apply(0, x)) / np.linalg.norm(pr.b)
+    assert rel <= 1e-10, rel
+    assert info["rel_res"] <= 1e-10
+    assert np.linalg.norm(x - x_or) <= tol_err * np.linalg.norm(x_or)
+
+
+@pytest.mark.parametrize("name", SMALL + ["ragged_3d_p2"])
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_fp64_solve_matches_oracle(name, use_graph):
+    pr = _problem(name)
+    x_or, info_or = OracleSolver.from_problem(pr).solve(pr.b, rtol=1e-10, maxiter=400)
+    assert info_or["status"] == 0
+    s = pkg.KCycleSolver(pr, precision="fp64", use_graph=use_graph)
+    x, info = s.solve(pr.b, rtol=1e-10, maxiter=400)
+    s.close()
+    assert info["status"] == 0, info
+    _check_solution(pr, x, info, x_or)
+    # the residual history is monotone within runs of RM calls
+    h, t = info["hist"], info["hist_type"]
+    assert np.all(np.diff(h)[t[1:] != 4] <= 1e-12 * h[0])
+
+
+@pytest.mark.parametrize("name", SMALL + ["ragged_3d_p2"])
+@pytest.mark.parametrize("precision", ["mixed", "mixed_bf16"])
+def test_mixed_precision_solve_matches_fp64_oracle(name, precision):
+    pr = _problem(name)
+    x_or, _ = OracleSolver.from_problem(pr).solve(pr.b, rtol=1e-10, maxiter=400)
+    s = pkg.KCycleSolver(pr, precision=precision, use_graph=True)
+    x, info = s.solve(pr.b, rtol=1e-10, maxiter=2000)
+    s.close()
+    assert info["status"] == 0, info
+    _check_solution(pr, x, info, x_or)
+    assert info["refinements"] >= 1
+
+
+def test_graph_and_eager_are_bitwise_identical_and_repeatable():
+    pr = workload("sipg3d_p2_8cube").make(5)
+    out = []
+    for g in (False, True, True):
+        s = pkg.KCycleSolver(pr, precision="fp64", use_graph=g)
+        x, info = s.solve(pr.b, rtol=1e-10)
+        x2, _ = s.solve(pr.b, rtol=1e-10)
+        s.close()
+        assert np.array_equal(x, x2)
+        out.append(x)
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[1], out[2])
+
+
+def test_device_and_host_inputs_agree():
+    pr = workload("sipg3d_p1_8x4x4").make(0)
+    s = pkg.KCycleSolver(pr, precision="fp64")
+    xh, _ = s.solve(pr.b, rtol=1e-10)
+    xd, _ = s.solve(torch.from_numpy(pr.b).cuda(), rtol=1e-10)
+    s.close()
+    assert np.array_equal(xh, xd.cpu().numpy())
+
+
+def test_degenerate_inputs():
+    pr = workload("sipg2d_p1_16x16").make(0)
+    s = pkg.KCycleSolver(pr, precision="fp64")
+    x, info = s.solve(np.zeros(pr.ndof), rtol=1e-10)          # b = 0: x = 0 at once
+    assert info["status"] == 0 and info["iters"] == 0 and not np.any(x)
+    xs, _ = s.solve(pr.b, rtol=1e-10)
+    x, info = s.solve(pr.b, x0=xs, rtol=0.0, atol=1e-6)        # x0 already converged
+    assert info["status"] == 0 and info["iters"] == 0 and np.array_equal(x, xs)
+    x, info = s.solve(pr.b, rtol=1e-10, maxiter=0)              # no iterations allowed
+    assert info["status"] == 1 and np.array_equal(x, np.zeros(pr.ndof))
+    x, info = s.solve(pr.b, rtol=1e-14, maxiter=2)              # not converged, no worse
+    assert info["status"] == 1 and info["rel_res"] < 1.0
+    bad = pr.b.copy()
+    bad[7] = np.nan
+    with pytest.raises(pkg.KcmgError) as e:
+        s.solve(bad, rtol=1e-10)
+    assert e.value.status == 3
+    s.close()
+
+
+def test_setup_rejects_bad_arguments():
+    pr = workload("sipg2d_p1_16x16").make(0)
+    p = pkg.kcmg_default_params(pr.d, pr.np_, (16, 10), 3)      # 10 not divisible by 4
+    with pytest.raises(pkg.KcmgError) as e:
+        pkg.kcmg_setup(p, pr.blocks, pr.prolong)
+    assert e.value.status == 5
+    blocks = pr.blocks.copy()
+    blocks[0, 3] = 0.0                                          # singular diagonal block
+    p = pkg.kcmg_default_params(pr.d, pr.np_, pr.n, 3)
+    with pytest.raises(pkg.KcmgError) as e:
+        pkg.kcmg_setup(p, blocks, pr.prolong)
+    assert e.value.status == 4
+
+
+def test_adjoint_solve():
+    pr = workload("sipg3d_p1_8x4x4").make(0)
+    s = pkg.KCycleSolver(pr, precision="fp64")
+    x, _ = s.solve(pr.b, rtol=1e-10)
+    lam, info = s.solve(pr.b, rtol=1e-10, adjoint=True)        # symmetric: same hierarchy
+    assert np.array_equal(x, lam) and info["status"] == 0
+    s.close()
+    blocks = pr.blocks.copy()
+    rng = np.random.default_rng(4)
+    for sl in range(1, blocks.shape[0]):
+        blocks[sl] *= 1.0 + 0.2 * rng.uniform(-1, 1, blocks.shape[1])[:, None, None]
+    A = dense_matrix(blocks, pr.nbr)
+    pr2 = make_problem(3, 1, (8, 4, 4), 3)
+    pr2.blocks = blocks
+    s = pkg.KCycleSolver(pr2, precision="fp64")
+    lam, info = s.solve(pr.b, rtol=1e-11, adjoint=True)
+    s.close()
+    ref = np.linalg.solve(A.T, pr.b)
+    assert info["status"] == 0
+    assert np.linalg.norm(lam - ref) <= 1e-8 * np.linalg.norm(ref)
+
+
+def test_gradient_kernel_matches_oracle():
+    pr = make_problem(3, 2, (8, 8, 4), 2, nu_kind="lognormal", seed=3)
+    s = pkg.KCycleSolver(pr, precision="fp64")
+    rng = np.random.default_rng(6)
+    lam, u = rng.standard_normal(pr.ndof), rng.standard_normal(pr.ndof)
+    g = s.grad_lognu(pr.nu, pr.ref, lam, u)
+    s.close()
+    assert _rel(g, grad_lognu(pr, pr.nu, lam, u)) < 1e-12

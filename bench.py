@@ -1,0 +1,349 @@
+#!/usr/bin/env python3
+"""DOFs solved per second to a relative residual of 1e-10 by the K-cycle orthonormalization
+multigrid (Alg. 2 with Alg. 1 after every correction, block-Jacobi smoother, level-local
+criteria of Sec. 4.2) on one GB300.
+
+Workload: 3-D SIPG p=2 (Np = 10) on 64^3 cells = 2,621,440 DOFs, coefficient 1000 inside a
+ball of radius 0.3 and 1 outside, zero Dirichlet, b iid U[-1,1] from the seed, 5-level
+2x2x2 agglomeration hierarchy, solved in FP64; the mixed forms (FP32 smoother sweeps,
+optionally BF16-stored block inverses, FP64 residual minimisation) are reported beside it.
+
+One step = one complete solve from x0 = 0 with inputs resident in device memory.  The
+operator (1.47 GB) is larger than the 129 MB L2, so no flush is needed between steps.
+Under torchrun every rank solves its own replica (seed = rank): the method has no
+data-parallel split on one node here ("replicas only"), so there is no collective.
+
+--impl reference times the CPU oracle (oracle/, plain single-threaded C) on the same
+workload: each step is a bounded sample (the first level-0 cycle), extrapolated to the full
+solve by the level-1 iteration count of the GPU solve.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "sipg3d_p2_64cube"
+RTOL = 1e-10
+LMAX = 60          # level-0 restart length of the benchmarked configuration
+MAXITER = 4000
+METRIC = "DOFs solved/s to 1e-10 rel. residual, mixed vs FP64; % of HBM roofline"
+UNIT = "DOF/s"
+# Level-1 iterations of the FP64 solve of this workload with LMAX = 60, measured on GB300;
+# the reference arm (a separate process) extrapolates its one-cycle sample with it.
+GPU_LEVEL1_ITERS_FP64 = 27582
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# FP64 FMA throughput of this GPU measured with a dependent-chain microbenchmark
+# (profiles/fp64_alu_peak_gb300.md): 1.198 TFLOP/s, i.e. 4.79 TB/s of operator data at
+# one FP64 FMA per 8-byte element.
+FP64_TFLOPS = 1.198
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [v.strip() for v in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_sample(pr, level1_total):
+    """Time the CPU oracle's first level-0 cycle of the solve and extrapolate to the full
+    solve by level-1 iterations (the dominant work).  Returns (dof_per_s, seconds, text)."""
+    import numpy as np
+
+    import oracle
+    t0 = time.perf_counter()
+    orc = oracle.OracleSolver.from_problem(pr, lmax=LMAX)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    x, info = orc.solve(pr.b, rtol=RTOL, maxiter=1)
+    t_cycle = time.perf_counter() - t0
+    l1 = max(1, int(info["level_iters"][1]))
+    t_full = t_cycle * level1_total / l1
+    txt = (f"first level-0 cycle of the solve ({l1} level-1 iterations) in {t_cycle:.2f} s "
+           f"(setup {t_setup:.1f} s, not counted), extrapolated to the {level1_total} level-1 "
+           f"iterations of the full solve: {t_full:.0f} s")
+    del orc, x
+    return pr.ndof / t_full, t_cycle, txt
+
+
+def run_reference(args, ws, rank):
+    from workloads import workload
+    if rank != 0:
+        return
+    pr = workload(WORKLOAD).make(0)
+    vals = []
+    txt = ""
+    for k in range(args.warmup + args.steps):
+        v, t, txt = oracle_sample(pr, GPU_LEVEL1_ITERS_FP64)
+        if k >= args.warmup:
+            vals.append((v, t))
+    value = statistics.median(v for v, _ in vals)
+    ms = statistics.median(t for _, t in vals) * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded SIPG workload)",
+            "config": {"workload": WORKLOAD, "dofs": pr.ndof, "rtol": RTOL, "lmax": LMAX},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": txt},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--maxiter", type=int, default=MAXITER,
+                    help="cap on level-0 cycles (profiling runs only; the benchmark solves to 1e-10)")
+    ap.add_argument("--workload", default=WORKLOAD, help="workload name (profiling runs only)")
+    ap.add_argument("--eager", action="store_true",
+                    help="host-driven loop control instead of the CUDA graph (same kernels; "
+                         "profilers see kernels inside conditional graph nodes only this way)")
+    args = ap.parse_args()
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_2512_08728_gb300 as pkg
+    from workloads import workload
+
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    pkg.build()
+    hbm_peak, peak_kind = _peaks()
+
+    pr = workload(args.workload).make(rank)
+    stream = torch.cuda.current_stream()
+    s = pkg.KCycleSolver(pr, precision="fp64", use_graph=not args.eager, lmax=LMAX,
+                         stream=stream.cuda_stream)
+    b = torch.from_numpy(pr.b).to(dev)
+    x = torch.zeros_like(b)
+
+    def solve(sv, bb, xx):
+        xx.zero_()
+        return pkg.kcmg_solve(sv.ctx, bb, xx, RTOL, 0.0, args.maxiter)
+
+    for _ in range(args.warmup):
+        info = solve(s, b, x)
+    s.kernel_report()   # reset the coarse-cycle counters
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = ClockSampler(dev)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    e0.record(stream)
+    for _ in range(args.steps):
+        infos.append(solve(s, b, x))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    value = ws * pr.ndof * args.steps / (ms * 1e-3)
+    status = [i["status"] for i in infos]
+    rel = max(i["rel_res"] for i in infos)
+    cycles = infos[-1]["iters"]
+    lvl = infos[-1]["level_iters"]
+    launches = sum(i["kernel_launches"] for i in infos)
+    rep = s.kernel_report(reps=10)
+
+    # roofline of the dominant kernel: the persistent coarse cycle (device timer + exact
+    # algorithmic bytes per launch, accumulated over the timed region)
+    cl = max(1, rep["coarse_launches"])
+    coarse_ms = rep["coarse_ms"] / cl
+    coarse_bytes = rep["coarse_bytes"] / cl
+    coarse_gbs = coarse_bytes / (coarse_ms * 1e-3) / 1e9 if coarse_ms > 0 else 0.0
+    share = rep["coarse_ms"] / ms if ms > 0 else 0.0
+    fp64_gbs = FP64_TFLOPS * 1e12 / 2 * 8 / 1e9
+    kernels = [
+        {"name": "k_coarse_cycle (levels 1-4, persistent)", "bound": "hbm",
+         "achieved": coarse_gbs, "peak": hbm_peak, "unit": "GB/s",
+         "frac": coarse_gbs / hbm_peak, "ms_per_launch": coarse_ms,
+         "bytes_per_launch": coarse_bytes, "share_of_step": share,
+         "ms_per_launch_by_level": [v / cl for v in rep["coarse_level_ms"][:pr.nlevels]]},
+        {"name": "k_spmv level 0 FP64 (Alg. 1 operator)", "bound": "alu",
+         "achieved": rep["spmv_bytes"] / (rep["spmv_ms"] * 1e-3) / 1e9,
+         "peak": fp64_gbs, "unit": "GB/s",
+         "frac": rep["spmv_bytes"] / (rep["spmv_ms"] * 1e-3) / 1e9 / fp64_gbs,
+         "ms_per_launch": rep["spmv_ms"], "bytes_per_launch": rep["spmv_bytes"]},
+        {"name": "k_bj_sweep level 0 FP64", "bound": "alu",
+         "achieved": rep["sweep_bytes"] / (rep["sweep_ms"] * 1e-3) / 1e9,
+         "peak": fp64_gbs, "unit": "GB/s",
+         "frac": rep["sweep_bytes"] / (rep["sweep_ms"] * 1e-3) / 1e9 / fp64_gbs,
+         "ms_per_launch": rep["sweep_ms"], "bytes_per_launch": rep["sweep_bytes"]},
+    ]
+
+    # end to end through the C interface with host buffers (copies inside the timing)
+    e2e = None
+    if not args.no_e2e:
+        bh = np.ascontiguousarray(pr.b)
+        xh = np.zeros(pr.ndof)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            xh[:] = 0.0
+            pkg.kcmg_solve(s.ctx, bh, xh, RTOL, 0.0, args.maxiter)
+        t_e2e = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([t_e2e], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = {"value": ws * pr.ndof * args.steps / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": 2 * pr.ndof * 8, "d2h_bytes_per_step": pr.ndof * 8}
+    s.close()
+
+    forms = {}
+    if not args.no_mixed:
+        for prec in ("mixed", "mixed_bf16"):
+            sm = pkg.KCycleSolver(pr, precision=prec, use_graph=True, lmax=LMAX,
+                                  stream=stream.cuda_stream)
+            pkg.kcmg_solve(sm.ctx, b, x, RTOL, 0.0, 2)   # capture the graph
+            sm.kernel_report()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            inf = [solve(sm, b, x) for _ in range(args.steps)]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            mms = e0.elapsed_time(e1)
+            rp = sm.kernel_report(reps=10)
+            sw_peak = hbm_peak
+            forms[prec] = {
+                "value": pr.ndof * args.steps / (mms * 1e-3), "unit": UNIT,
+                "ms_per_step": mms / args.steps, "status": [i["status"] for i in inf],
+                "rel_res": max(i["rel_res"] for i in inf), "cycles": inf[-1]["iters"],
+                "dtype": "f32 smoother sweeps" + (", bf16 block inverses" if prec == "mixed_bf16" else "")
+                         + "; f64 residual minimisation, transfers, coarsest solve",
+                "smoother_sweep": {"bound": "hbm", "achieved": rp["sweep_bytes"] / (rp["sweep_ms"] * 1e-3) / 1e9,
+                                   "peak": sw_peak, "unit": "GB/s",
+                                   "frac": rp["sweep_bytes"] / (rp["sweep_ms"] * 1e-3) / 1e9 / sw_peak},
+                "coarse_cycle_gbs": (rp["coarse_bytes"] / max(1, rp["coarse_launches"]))
+                                    / (rp["coarse_ms"] / max(1, rp["coarse_launches"]) * 1e-3) / 1e9
+                                    if rp["coarse_ms"] > 0 else None}
+            sm.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, t, txt = oracle_sample(pr, int(lvl[1]))
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": txt}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded SIPG workload)",
+            "config": {"workload": args.workload, "cells": list(pr.n), "p": pr.p, "dofs": pr.ndof,
+                       "levels": pr.nlevels, "nu_ratio": 1000, "smoother": "block-Jacobi omega 0.7, 5 sweeps",
+                       "rtol": RTOL, "lmax": LMAX, "cuda_graph": not args.eager, "coarse_cycle": "persistent",
+                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (operator 1.47 GB vs 129 MB L2): no flush"},
+            "status": status, "rel_res": rel, "cycles": cycles, "level_iters": lvl[:pr.nlevels],
+            "roofline": {"bound": kernels[0]["bound"], "achieved": kernels[0]["achieved"],
+                         "peak": hbm_peak, "unit": "GB/s", "frac": kernels[0]["frac"],
+                         "traffic": None, "peak_kind": peak_kind,
+                         "kernel": kernels[0]["name"]},
+            "kernels": kernels,
+            "forms": forms,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

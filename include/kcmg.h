@@ -83,6 +83,9 @@ typedef struct {
     int precision;           /* kcmg_precision */
     int use_graph;           /* 1: run the cycle as a CUDA graph with conditional while
                                 nodes; 0: host-driven control (reads a flag per loop test) */
+    int coarse_persistent;   /* 1: every level below the finest runs in one persistent
+                                cooperative kernel per finest-level cycle; 0: one kernel
+                                per step (nested loops as conditional graph nodes) */
 } kcmg_params;
 
 /* Fill p with the defaults of Sec. 4.2 / Alg. BJ for the given sizes (blocks, prolong
@@ -100,6 +103,7 @@ typedef struct {
                                            level 0 (restarts + 1), i.e. refinement steps */
     double res0;                        /* ||b - A x0|| */
     double rel_res;                     /* ||b - A x|| / res0, FP64 true residual */
+    long long kernel_launches;          /* kernels launched by the solve (-1: unknown) */
     int hist_cap, hist_len;
     double *hist;
     int *hist_type;
@@ -152,6 +156,17 @@ kcmg_status kcmg_get_blocks(kcmg_ctx *ctx, int level, double *out);
    final x and r (recursive residual) and the basis size in *l. */
 kcmg_status kcmg_rm_sequence(kcmg_ctx *ctx, int level, const double *b, const double *x0,
                              const double *z, int ncorr, double *x, double *r, int *l);
+
+/* Measurement support (no counterpart in the paper).  out[0..2]: launches, total device
+   milliseconds (GPU global timer, entry to last barrier) and algorithmic bytes (unique
+   operator and vector bytes of every phase) of the persistent coarse-cycle kernel since
+   the previous call; the counters are then reset.  If reps > 0 also times, with CUDA events
+   on the library's stream, reps launches each of the level-0 FP64 operator application
+   (out[3] ms per launch, out[4] algorithmic bytes) and of one full block-Jacobi sweep in
+   the smoother's precision (out[5] ms, out[6] bytes).  out[7 + l] (if nout allows): device
+   milliseconds the coarse-cycle kernel spent on level l (the coarsest: its direct solves).
+   nout >= 7. */
+kcmg_status kcmg_kernel_report(kcmg_ctx *ctx, int reps, double *out, int nout);
 
 /* Level sizes: number of cells of a level (0 if out of range). */
 int kcmg_level_cells(const kcmg_ctx *ctx, int level);

@@ -28,8 +28,7 @@ struct Level {
   __nv_bfloat16* D16 = nullptr;
   void *x = nullptr, *r = nullptr, *b = nullptr, *z = nullptr, *t = nullptr, *w = nullptr,
        *wre = nullptr, *W = nullptr, *Z = nullptr;
-  // mixed form, level 0 only: FP32 copies for the smoother sweeps (the level's own
-  // vectors are FP64 there)
+  // mixed forms: FP32 buffers of the smoother sweeps (the level's vectors are FP64)
   float *r_lo = nullptr, *z_lo = nullptr, *t_lo = nullptr;
   int lcap = 0;
   int nblk = 1;                     // blocks of the vector / dot kernels
@@ -60,6 +59,17 @@ struct kcmg_ctx {
   int* dflag = nullptr;
   cudaGraphExec_t gexec = nullptr;
   bool graph_ready = false;
+  // persistent coarse cycle (levels >= 1 in one cooperative launch per level-0 cycle)
+  bool coarse_kernel = false;
+  int cc_grid = 0;
+  CoarseArgs cc{};
+  long long graph_body_launches = 0;  // kernels per level-0 loop body of the graph
+  long long last_launches = 0;        // kernels of the last cycle run
+  // coarse-cycle counters (launches, ns, algorithmic bytes) and report scratch
+  unsigned long long* stat_ns = nullptr;
+  unsigned long long* stat_launches = nullptr;
+  double* stat_bytes = nullptr;
+  unsigned long long* stat_level_ns = nullptr;
   kcmg_ctx* adj = nullptr;       // transposed hierarchy (may be this)
   bool adj_built = false;
   std::vector<void*> allocs;
@@ -227,15 +237,26 @@ void build_hierarchy(kcmg_ctx* ctx, const double* blocks_src) {
 }
 
 // ------------------------------------------------------------------ the cycle
-// Level 0 keeps its vectors, basis and residual minimisation in T0 (= FP64); every other
-// level, and the smoother sweeps and transfers of level 0, work in T.  T = double is the
-// FP64 form; T = float the mixed form, where the FP64 residual minimisation of level 0
-// over FP32-computed corrections acts as the iterative refinement.
+// Every level keeps its vectors, basis W, Z and residual minimisation (Alg. 1, with the
+// FP64 operator) in T0 = FP64, as do the transfers and the coarsest solve; the smoother
+// sweeps run in T.  T = double is the FP64 form; T = float the mixed form, in which the
+// FP64 residual minimisation over FP32-smoothed corrections acts as the iterative
+// refinement (the attainable residual is FP64's).
+void launch_coarse(kcmg_ctx* ctx, cudaStream_t s) {
+  cudaError_t err;
+  if (!ctx->mixed) err = launch_coarse_cycle<double, double>(ctx->cc, ctx->cc_grid, ctx->lv[1].block_rows, s);
+  else if (ctx->p.precision == KCMG_MIXED_BF16INV)
+    err = launch_coarse_cycle<float, __nv_bfloat16>(ctx->cc, ctx->cc_grid, ctx->lv[1].block_rows, s);
+  else err = launch_coarse_cycle<float, float>(ctx->cc, ctx->cc_grid, ctx->lv[1].block_rows, s);
+  CK(err);
+}
+
 template <typename T0, typename T>
 struct Cycle {
   kcmg_ctx* ctx;
   bool capture = false;
   cudaGraphConditionalHandle handle[KCMG_MAX_LEVELS] = {};
+  long long launches = 0;   // kernels issued (eager) or recorded (capture)
 
   static constexpr bool kMixed = !std::is_same<T0, T>::value;
 
@@ -265,6 +286,7 @@ struct Cycle {
     T* buf[2] = {z, t};
     const double om = ctx->p.omega;
     const int sw = ctx->p.sweeps;
+    launches += sw;
     for (int k = 0; k < sw; ++k) {
       T* out = buf[k & 1];
       const T* old = buf[(k + 1) & 1];
@@ -289,7 +311,8 @@ struct Cycle {
   template <typename V>
   V* smooth(int lev, const V* r, cudaStream_t s) {
     Level& L = ctx->lv[lev];
-    if (kMixed && lev == 0) {
+    if (kMixed) {
+      launches += 2;
       launch_convert<double, float>((const double*)r, L.r_lo, L.N, s);
       const float* out = (const float*)sweeps(L, (const T*)L.r_lo, (T*)L.z_lo, (T*)L.t_lo, s);
       launch_convert<float, double>(out, (double*)L.z, L.N, s);
@@ -307,6 +330,7 @@ struct Cycle {
     V* w = static_cast<V*>(L.w);
     V* wre = static_cast<V*>(L.wre);
     EpiArgs none = epi(lev, EPI_NONE);
+    launches += 6;
     launch_spmv<V>(ctx->np, ctx->dim, Aop, L.nbr, L.N, L.G, L.rows_pad, L.block_rows, z, w,
                    nullptr, L.partial, none, 0, s);
     launch_gram_dots<V>(W, L.N, w, L.lcap, L.nblk, L.partial, epi(lev, EPI_GRAM1), 0, s);
@@ -328,10 +352,18 @@ struct Cycle {
     Level& C = ctx->lv[lev + 1];
     V* z = smooth<V>(lev, static_cast<V*>(L.r), s);                       // pre-smoother
     rm<V>(lev, Aop, z, 0, 1, s);
+    launches += 3;                                                         // transfers, restart check
     if (lev + 1 == ctx->nlev - 1) {                                        // direct solve
-      launch_restrict<T, V>(ctx->np, ctx->dim, L.n, C.n, Pm(), static_cast<V*>(L.r),
-                            static_cast<T*>(C.b), nullptr, nullptr, nullptr, EpiArgs{}, s);
-      launch_coarse_gemv<T>(ctx->Ainv, ctx->Nc, static_cast<T*>(C.b), static_cast<T*>(C.x), s);
+      launches += 1;
+      launch_restrict<V, V>(ctx->np, ctx->dim, L.n, C.n, ctx->P64, static_cast<V*>(L.r),
+                            static_cast<V*>(C.b), nullptr, nullptr, nullptr, EpiArgs{}, s);
+      launch_coarse_gemv<V>(ctx->Ainv, ctx->Nc, static_cast<V*>(C.b), static_cast<V*>(C.x), s);
+    } else if (lev == 0 && ctx->coarse_kernel) {                           // levels >= 1 in
+      launch_restrict<V, V>(ctx->np, ctx->dim, L.n, C.n, ctx->P64, static_cast<V*>(L.r),  // one
+                            static_cast<V*>(C.b), static_cast<V*>(C.r), static_cast<V*>(C.x),  // launch
+                            nullptr, EpiArgs{}, s);
+      launches += 1;
+      launch_coarse(ctx, s);
     } else {                                                               // recursion
       if (capture) {
         cudaGraph_t g;
@@ -343,12 +375,12 @@ struct Cycle {
         CK(cudaStreamGetCaptureInfo(s, &cs, &id, &g, &deps, &ed, &nd));
         CK(cudaGraphConditionalHandleCreate(&handle[lev + 1], g, 0, 0));
       }
-      launch_restrict<T, V>(ctx->np, ctx->dim, L.n, C.n, Pm(), static_cast<V*>(L.r),
-                            static_cast<T*>(C.b), static_cast<T*>(C.r), static_cast<T*>(C.x),
+      launch_restrict<V, V>(ctx->np, ctx->dim, L.n, C.n, ctx->P64, static_cast<V*>(L.r),
+                            static_cast<V*>(C.b), static_cast<V*>(C.r), static_cast<V*>(C.x),
                             C.partial, epi(lev + 1, EPI_MG_BEGIN), s);
-      loop<T>(lev + 1, Ainner(C), s);
+      loop<V>(lev + 1, (const V*)C.A64, s);
     }
-    launch_prolong<T, V>(ctx->np, ctx->dim, L.n, C.n, Pm(), static_cast<T*>(C.x),
+    launch_prolong<V, V>(ctx->np, ctx->dim, L.n, C.n, ctx->P64, static_cast<V*>(C.x),
                          static_cast<V*>(L.z), s);                         // z = P z_c
     rm<V>(lev, Aop, static_cast<V*>(L.z), 0, 2, s);
     z = smooth<V>(lev, static_cast<V*>(L.r), s);                           // post-smoother
@@ -358,6 +390,8 @@ struct Cycle {
                    static_cast<V*>(L.x), static_cast<V*>(L.r), static_cast<V*>(L.b), L.partial,
                    epi(lev, EPI_RESTART), 1, s);
   }
+
+  long long body_launches = 0;   // level-0 loop body (capture)
 
   bool read_cond(int lev) {
     int c = 0;
@@ -391,7 +425,9 @@ struct Cycle {
     cudaStream_t bs = ctx->cap[lev + 1];
     CK(cudaStreamBeginCaptureToGraph(bs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                      cudaStreamCaptureModeRelaxed));
+    const long long before = launches;
     body<V>(lev, Aop, bs);
+    if (lev == 0) body_launches = launches - before;
     CK(cudaStreamEndCapture(bs, nullptr));
   }
 
@@ -436,12 +472,16 @@ void init_states(kcmg_ctx* ctx, double rtol0, double atol0, int maxit0) {
     h.atol = (l == 0) ? atol0 : 0.0;
     h.status = KCMG_OK;
     h.hist_cap = (l == 0) ? ctx->hist_cap : 0;
-    // breakdown threshold of Alg. 1 relative to ||A z||, by the level's precision
-    h.brk = (l == 0 || !ctx->mixed) ? 1e-14 : 1e-6;
+    // breakdown threshold of Alg. 1 relative to ||A z|| (the minimisation is FP64)
+    h.brk = 1e-14;
     h.guard = 0;
     h.guard_cap = (int)cap;
     if (!ctx->lv[l].st) continue;   // the coarsest level is solved directly: no state
     CK(cudaMemcpyAsync(ctx->lv[l].st, &h, sizeof h, cudaMemcpyHostToDevice, ctx->s));
+  }
+  if (ctx->coarse_kernel) {   // grid-barrier counter and error flag of the coarse cycle
+    CK(cudaMemsetAsync(ctx->cc.bar_count, 0, sizeof(unsigned int), ctx->s));
+    CK(cudaMemsetAsync(ctx->cc.err, 0, sizeof(int), ctx->s));
   }
   CK(cudaStreamSynchronize(ctx->s));
 }
@@ -452,6 +492,7 @@ void run_cycle(kcmg_ctx* ctx) {
     if (!ctx->graph_ready) {
       Cycle<double, T> cy{ctx};
       cy.capture = true;
+      ctx->graph_body_launches = 0;
       cudaGraph_t g;
       CK(cudaStreamBeginCapture(ctx->s, cudaStreamCaptureModeRelaxed));
       try {
@@ -462,14 +503,19 @@ void run_cycle(kcmg_ctx* ctx) {
         throw;
       }
       CK(cudaStreamEndCapture(ctx->s, &g));
+      // kernel launches per execution: exact when the levels below 0 run in one kernel
+      ctx->graph_body_launches = ctx->coarse_kernel ? cy.body_launches : -1;
       CK(cudaGraphInstantiate(&ctx->gexec, g, 0));
       CK(cudaGraphDestroy(g));
       ctx->graph_ready = true;
     }
     CK(cudaGraphLaunch(ctx->gexec, ctx->s));
+    ctx->last_launches = -2;   // filled from the cycle count after the solve
   } else {
     Cycle<double, T> cy{ctx};
+    cy.launches = 1;           // the initial residual
     cy.run(ctx->s);
+    ctx->last_launches = cy.launches;
   }
   CK(cudaGetLastError());
 }
@@ -512,6 +558,11 @@ void fill_info(kcmg_ctx* ctx, kcmg_info* info, const StateReport& rep, double re
   info->refinements = ctx->mixed ? rep.st[0].nrestart + 1 : 0;
   info->res0 = res0;
   info->rel_res = rel;
+  if (ctx->last_launches == -2)   // graph: begin + cycles x body + final residual
+    info->kernel_launches = ctx->graph_body_launches < 0 ? -1
+                            : 2 + (long long)rep.st[0].guard * ctx->graph_body_launches;
+  else
+    info->kernel_launches = ctx->last_launches + 1;
   const int hl = rep.st[0].hist_len;
   info->hist_len = 0;
   if (info->hist && info->hist_type && info->hist_cap > 0) {
@@ -536,6 +587,15 @@ kcmg_status solve_impl(kcmg_ctx* ctx, const double* b, double* x, double rtol, d
   if (ctx->mixed) run_cycle<float>(ctx);
   else run_cycle<double>(ctx);
   read_states(ctx, rep);
+  if (ctx->coarse_kernel) {
+    int bar_err = 0;
+    CK(cudaMemcpyAsync(&bar_err, ctx->cc.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    if (bar_err) {
+      set_err(ctx, "coarse cycle: a grid barrier timed out; the result is invalid");
+      return KCMG_CUDA_ERROR;
+    }
+  }
   const double rn = fp64_residual(ctx, static_cast<double*>(L.x), static_cast<double*>(L.b), ctx->ro);
   const double r0 = rep.st[0].rnorm0;
   copy_out(ctx, x, static_cast<double*>(L.x), N);
@@ -569,6 +629,7 @@ void kcmg_default_params(kcmg_params* p, int dim, int np, const int n[3], int nl
   p->lmax = 0;
   p->precision = KCMG_FP64;
   p->use_graph = 1;
+  p->coarse_persistent = 1;
 }
 
 const char* kcmg_status_string(kcmg_status s) {
@@ -625,7 +686,8 @@ kcmg_ctx* build_ctx(const kcmg_params* p, cudaStream_t user, const double* block
   ctx->p = *p;
   try {
     REQUIRE(p->dim == 2 || p->dim == 3, "dim must be 2 or 3");
-    REQUIRE(np_supported(p->np), "unsupported np %d (3, 4, 6, 10, 20)", p->np);
+    REQUIRE(np_supported(p->np, p->dim), "unsupported np %d for dim %d (2-D: 3, 6, 10; 3-D: 4, 10, 20)",
+            p->np, p->dim);
     REQUIRE(p->nlevels >= 2 && p->nlevels <= KCMG_MAX_LEVELS, "nlevels must be in [2, %d]", KCMG_MAX_LEVELS);
     REQUIRE(p->blocks && p->prolong, "blocks and prolong must be set");
     REQUIRE(p->sweeps >= 1 && p->sweeps <= 64, "sweeps must be in [1, 64]");
@@ -674,21 +736,88 @@ kcmg_ctx* build_ctx(const kcmg_params* p, cudaStream_t user, const double* block
         const size_t per = (size_t)2 * ctx->lv[0].N * sizeof(double);
         while (cap > 16 && (size_t)cap * per > fr / 3) cap /= 2;
       }
-      // level 0 is FP64 in both forms; the mixed form runs every other level in FP32
-      if (ctx->mixed && l > 0) alloc_cycle_vectors<float>(ctx, ctx->lv[l], cap);
-      else alloc_cycle_vectors<double>(ctx, ctx->lv[l], cap);
-      if (ctx->mixed && l == 0) {
-        Level& L0 = ctx->lv[0];
-        L0.r_lo = dalloc<float>(ctx, L0.N);
-        L0.z_lo = dalloc<float>(ctx, L0.N);
-        L0.t_lo = dalloc<float>(ctx, L0.N);
+      alloc_cycle_vectors<double>(ctx, ctx->lv[l], cap);
+      if (ctx->mixed) {   // FP32 smoother buffers
+        Level& Lm = ctx->lv[l];
+        Lm.r_lo = dalloc<float>(ctx, Lm.N);
+        Lm.z_lo = dalloc<float>(ctx, Lm.N);
+        Lm.t_lo = dalloc<float>(ctx, Lm.N);
       }
     }
     {  // coarsest level: b (restricted residual) and x (direct solution) only
       Level& C = ctx->lv[ctx->nlev - 1];
-      const size_t es = ctx->mixed ? sizeof(float) : sizeof(double);
-      C.b = dalloc<unsigned char>(ctx, C.N * es);
-      C.x = dalloc<unsigned char>(ctx, C.N * es);
+      C.b = dalloc<double>(ctx, C.N);
+      C.x = dalloc<double>(ctx, C.N);
+    }
+    // persistent coarse cycle for levels >= 1 (needs at least one iterated coarse level)
+    ctx->coarse_kernel = p->coarse_persistent && ctx->nlev > 2;
+    if (ctx->coarse_kernel) {
+      for (int l = 1; l < ctx->nlev - 1; ++l)
+        REQUIRE(ctx->lv[l].lcap + 1 <= kCoarseMaxCols,
+                "level %d keeps %d basis vectors; the persistent coarse cycle supports %d",
+                l, ctx->lv[l].lcap, kCoarseMaxCols - 1);
+      int grid = 0;
+      const int thr = ctx->lv[1].block_rows;
+      cudaError_t ge;
+      if (!ctx->mixed) ge = coarse_cycle_grid<double, double>(ctx->np, ctx->dim, thr, &grid);
+      else if (p->precision == KCMG_MIXED_BF16INV) ge = coarse_cycle_grid<float, __nv_bfloat16>(ctx->np, ctx->dim, thr, &grid);
+      else ge = coarse_cycle_grid<float, float>(ctx->np, ctx->dim, thr, &grid);
+      CK(ge);
+      ctx->cc_grid = grid;
+      CoarseArgs& a = ctx->cc;
+      memset(&a, 0, sizeof a);
+      a.lev0 = 1;
+      a.nlev = ctx->nlev;
+      a.dim = ctx->dim;
+      a.np = ctx->np;
+      a.P = ctx->P64;
+      a.omega = p->omega;
+      a.sweeps = p->sweeps;
+      a.lmax = p->lmax;
+      a.brk = 1e-14;
+      a.partial_stride = (size_t)grid * kCoarseMaxCols;
+      a.partial = dalloc<double>(ctx, 2 * a.partial_stride);
+      a.red = dalloc<double>(ctx, kCoarseMaxCols);
+      a.bar_count = dalloc<unsigned int>(ctx, 1);
+      a.bar_gen = dalloc<unsigned int>(ctx, 1);
+      a.err = dalloc<int>(ctx, 1);
+      CK(cudaMemsetAsync(a.bar_gen, 0, sizeof(unsigned int), ctx->s));
+      for (int l = 1; l < ctx->nlev; ++l) {
+        Level& L = ctx->lv[l];
+        CoarseLevel& c = a.lv[l];
+        c.A = L.A64;                                                  // Alg. 1 operator
+        c.As = ctx->mixed ? (const void*)L.A32 : (const void*)L.A64;  // smoother operator
+        c.Dinv = !ctx->mixed ? (const void*)L.D64 : L.D16 ? (const void*)L.D16 : (const void*)L.D32;
+        c.s0 = ctx->mixed ? (void*)L.z_lo : L.t;                      // smoother scratch
+        c.s1 = ctx->mixed ? (void*)L.t_lo : L.wre;
+        c.nbr = L.nbr;
+        for (int j = 0; j < 3; ++j) c.n[j] = L.n[j];
+        c.N = L.N;
+        c.G = L.G;
+        c.rows_pad = L.rows_pad;
+        c.x = L.x; c.r = L.r; c.b = L.b; c.z = L.z; c.t = L.t; c.w = L.w; c.wre = L.wre;
+        c.W = L.W; c.Z = L.Z;
+        c.lcap = L.lcap;
+        c.maxit = p->lvl_maxit[l];
+        c.rtol = p->lvl_rtol[l];
+        c.st = L.st;
+      }
+      a.Ainv = ctx->Ainv;
+      a.Nc = ctx->Nc;
+      ctx->stat_ns = dalloc<unsigned long long>(ctx, 1);
+      ctx->stat_launches = dalloc<unsigned long long>(ctx, 1);
+      ctx->stat_bytes = dalloc<double>(ctx, 1);
+      ctx->stat_level_ns = dalloc<unsigned long long>(ctx, KCMG_MAX_LEVELS);
+      CK(cudaMemsetAsync(ctx->stat_level_ns, 0, 8 * KCMG_MAX_LEVELS, ctx->s));
+      a.stat_level_ns = ctx->stat_level_ns;
+      CK(cudaMemsetAsync(ctx->stat_ns, 0, 8, ctx->s));
+      CK(cudaMemsetAsync(ctx->stat_launches, 0, 8, ctx->s));
+      CK(cudaMemsetAsync(ctx->stat_bytes, 0, 8, ctx->s));
+      a.stat_ns = ctx->stat_ns;
+      a.stat_launches = ctx->stat_launches;
+      a.stat_bytes = ctx->stat_bytes;
+      a.smoother_bytes = ctx->mixed ? 4 : 8;
+      a.inverse_bytes = !ctx->mixed ? 8 : (p->precision == KCMG_MIXED_BF16INV ? 2 : 4);
     }
     const size_t N0 = ctx->lv[0].N;
     ctx->ro = dalloc<double>(ctx, N0);
@@ -709,8 +838,8 @@ kcmg_ctx* build_ctx(const kcmg_params* p, cudaStream_t user, const double* block
   }
 }
 
-// vectors of a level are FP64 on level 0 and in both forms' FP64 levels, FP32 otherwise
-bool level_is_f32(const kcmg_ctx* ctx, int lev) { return ctx->mixed && lev > 0; }
+// vectors of every level are FP64 (only the smoother sweeps use the inner precision)
+bool level_is_f32(const kcmg_ctx*, int) { return false; }
 
 // FP64 user vector -> level buffer of the level's type
 void load_vec(kcmg_ctx* ctx, int lev, void* dst, const double* src, size_t n) {
@@ -840,8 +969,7 @@ kcmg_status kcmg_smooth(kcmg_ctx* ctx, int level, const double* r, double* z) {
     const void* out;
     if (ctx->mixed) {
       Cycle<double, float> cy{ctx};
-      if (level == 0) out = cy.smooth<double>(0, static_cast<double*>(L.b), ctx->s);
-      else out = cy.smooth<float>(level, static_cast<float*>(L.b), ctx->s);
+      out = cy.smooth<double>(level, static_cast<double*>(L.b), ctx->s);
     } else {
       Cycle<double, double> cy{ctx};
       out = cy.smooth<double>(level, static_cast<double*>(L.b), ctx->s);
@@ -857,15 +985,8 @@ kcmg_status kcmg_restrict(kcmg_ctx* ctx, int level, const double* r, double* rc)
     REQUIRE(level >= 0 && level < ctx->nlev - 1 && r && rc, "bad level or null vector");
     Level &L = ctx->lv[level], &C = ctx->lv[level + 1];
     load_vec(ctx, level, L.t, r, L.N);
-    if (!ctx->mixed)
-      launch_restrict<double, double>(ctx->np, ctx->dim, L.n, C.n, ctx->P64, static_cast<double*>(L.t),
-                                      static_cast<double*>(C.b), nullptr, nullptr, nullptr, EpiArgs{}, ctx->s);
-    else if (level == 0)
-      launch_restrict<float, double>(ctx->np, ctx->dim, L.n, C.n, ctx->P32, static_cast<double*>(L.t),
-                                     static_cast<float*>(C.b), nullptr, nullptr, nullptr, EpiArgs{}, ctx->s);
-    else
-      launch_restrict<float, float>(ctx->np, ctx->dim, L.n, C.n, ctx->P32, static_cast<float*>(L.t),
-                                    static_cast<float*>(C.b), nullptr, nullptr, nullptr, EpiArgs{}, ctx->s);
+    launch_restrict<double, double>(ctx->np, ctx->dim, L.n, C.n, ctx->P64, static_cast<double*>(L.t),
+                                    static_cast<double*>(C.b), nullptr, nullptr, nullptr, EpiArgs{}, ctx->s);
     CK(cudaGetLastError());
     store_vec(ctx, level + 1, rc, C.b, C.N);
     return KCMG_OK;
@@ -877,15 +998,8 @@ kcmg_status kcmg_prolong(kcmg_ctx* ctx, int level, const double* zc, double* z) 
     REQUIRE(level >= 0 && level < ctx->nlev - 1 && zc && z, "bad level or null vector");
     Level &L = ctx->lv[level], &C = ctx->lv[level + 1];
     load_vec(ctx, level + 1, C.x, zc, C.N);
-    if (!ctx->mixed)
-      launch_prolong<double, double>(ctx->np, ctx->dim, L.n, C.n, ctx->P64, static_cast<double*>(C.x),
-                                     static_cast<double*>(L.t), ctx->s);
-    else if (level == 0)
-      launch_prolong<float, double>(ctx->np, ctx->dim, L.n, C.n, ctx->P32, static_cast<float*>(C.x),
-                                    static_cast<double*>(L.t), ctx->s);
-    else
-      launch_prolong<float, float>(ctx->np, ctx->dim, L.n, C.n, ctx->P32, static_cast<float*>(C.x),
-                                   static_cast<float*>(L.t), ctx->s);
+    launch_prolong<double, double>(ctx->np, ctx->dim, L.n, C.n, ctx->P64, static_cast<double*>(C.x),
+                                   static_cast<double*>(L.t), ctx->s);
     CK(cudaGetLastError());
     store_vec(ctx, level, z, L.t, L.N);
     return KCMG_OK;
@@ -921,7 +1035,7 @@ template <typename T0, typename T, typename V>
 void rm_sequence_impl(kcmg_ctx* ctx, int level, const double* z, int ncorr) {
   Level& L = ctx->lv[level];
   Cycle<T0, T> cy{ctx};
-  const V* Aop = (level == 0) ? (const V*)L.A64 : (const V*)cy.Ainner(L);
+  const V* Aop = (const V*)L.A64;
   launch_spmv<V>(ctx->np, ctx->dim, Aop, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
                  static_cast<V*>(L.x), static_cast<V*>(L.r), static_cast<V*>(L.b), L.partial,
                  cy.epi(level, EPI_MG_BEGIN), 0, ctx->s);
@@ -945,8 +1059,7 @@ kcmg_status kcmg_rm_sequence(kcmg_ctx* ctx, int level, const double* b, const do
     load_vec(ctx, level, L.b, b, L.N);
     load_vec(ctx, level, L.x, x0, L.N);
     if (!ctx->mixed) rm_sequence_impl<double, double, double>(ctx, level, z, ncorr);
-    else if (level == 0) rm_sequence_impl<double, float, double>(ctx, level, z, ncorr);
-    else rm_sequence_impl<double, float, float>(ctx, level, z, ncorr);
+    else rm_sequence_impl<double, float, double>(ctx, level, z, ncorr);
     CK(cudaGetLastError());
     store_vec(ctx, level, x, L.x, L.N);
     store_vec(ctx, level, r, L.r, L.N);
@@ -954,6 +1067,82 @@ kcmg_status kcmg_rm_sequence(kcmg_ctx* ctx, int level, const double* b, const do
     CK(cudaMemcpyAsync(&h, L.st, sizeof h, cudaMemcpyDeviceToHost, ctx->s));
     CK(cudaStreamSynchronize(ctx->s));
     *l = h.l;
+    return KCMG_OK;
+  });
+}
+
+kcmg_status kcmg_kernel_report(kcmg_ctx* ctx, int reps, double* out, int nout) {
+  return guarded(ctx, [&]() -> kcmg_status {
+    REQUIRE(out && nout >= 7 && reps >= 0, "kcmg_kernel_report needs out[7] and reps >= 0");
+    for (int i = 0; i < nout; ++i) out[i] = 0.0;
+    if (ctx->coarse_kernel) {
+      unsigned long long ns = 0, nl = 0;
+      double by = 0;
+      CK(cudaMemcpyAsync(&ns, ctx->stat_ns, 8, cudaMemcpyDeviceToHost, ctx->s));
+      CK(cudaMemcpyAsync(&nl, ctx->stat_launches, 8, cudaMemcpyDeviceToHost, ctx->s));
+      CK(cudaMemcpyAsync(&by, ctx->stat_bytes, 8, cudaMemcpyDeviceToHost, ctx->s));
+      unsigned long long lns[KCMG_MAX_LEVELS] = {0};
+      CK(cudaMemcpyAsync(lns, ctx->stat_level_ns, sizeof lns, cudaMemcpyDeviceToHost, ctx->s));
+      CK(cudaMemsetAsync(ctx->stat_level_ns, 0, sizeof lns, ctx->s));
+      CK(cudaStreamSynchronize(ctx->s));
+      for (int l = 0; l < KCMG_MAX_LEVELS && 7 + l < nout; ++l) out[7 + l] = lns[l] * 1e-6;
+      CK(cudaMemsetAsync(ctx->stat_ns, 0, 8, ctx->s));
+      CK(cudaMemsetAsync(ctx->stat_launches, 0, 8, ctx->s));
+      CK(cudaMemsetAsync(ctx->stat_bytes, 0, 8, ctx->s));
+      CK(cudaStreamSynchronize(ctx->s));
+      out[0] = (double)nl;
+      out[1] = ns * 1e-6;
+      out[2] = by;
+    }
+    if (reps > 0) {
+      Level& L = ctx->lv[0];
+      const int S = ctx->S, np = ctx->np;
+      cudaEvent_t e0, e1;
+      CK(cudaEventCreate(&e0));
+      CK(cudaEventCreate(&e1));
+      CK(cudaMemsetAsync(L.b, 0, L.N * sizeof(double), ctx->s));
+      CK(cudaMemsetAsync(L.t, 0, L.N * sizeof(double), ctx->s));
+      EpiArgs none;
+      // FP64 operator (Alg. 1 SpMV on level 0)
+      CK(cudaEventRecord(e0, ctx->s));
+      for (int k = 0; k < reps; ++k)
+        launch_spmv<double>(np, ctx->dim, L.A64, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
+                            static_cast<double*>(L.t), static_cast<double*>(L.w), nullptr, nullptr, none, 0, ctx->s);
+      CK(cudaEventRecord(e1, ctx->s));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      out[3] = ms / reps;
+      out[4] = (double)S * L.N * np * 8 + 2.0 * L.N * 8;
+      // one full block-Jacobi sweep on level 0 in the smoother's precision
+      const double sb = ctx->mixed ? 4 : 8;
+      const double ib = !ctx->mixed ? 8 : (L.D16 ? 2 : 4);
+      if (ctx->mixed) {
+        CK(cudaMemsetAsync(L.r_lo, 0, L.N * sizeof(float), ctx->s));
+        CK(cudaMemsetAsync(L.t_lo, 0, L.N * sizeof(float), ctx->s));
+      }
+      CK(cudaEventRecord(e0, ctx->s));
+      for (int k = 0; k < reps; ++k) {
+        if (!ctx->mixed)
+          launch_bj_sweep<double, double>(np, ctx->dim, L.A64, L.D64, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
+                                          static_cast<double*>(L.b), static_cast<double*>(L.t),
+                                          static_cast<double*>(L.z), ctx->p.omega, 0, ctx->s);
+        else if (L.D16)
+          launch_bj_sweep<float, __nv_bfloat16>(np, ctx->dim, L.A32, L.D16, L.nbr, L.N, L.G, L.rows_pad,
+                                                L.block_rows, L.r_lo, L.t_lo, L.z_lo, ctx->p.omega, 0, ctx->s);
+        else
+          launch_bj_sweep<float, float>(np, ctx->dim, L.A32, L.D32, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
+                                        L.r_lo, L.t_lo, L.z_lo, ctx->p.omega, 0, ctx->s);
+      }
+      CK(cudaEventRecord(e1, ctx->s));
+      CK(cudaEventSynchronize(e1));
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      out[5] = ms / reps;
+      out[6] = (double)(S - 1) * L.N * np * sb + (double)L.N * np * ib + 3.0 * L.N * sb;
+      CK(cudaGetLastError());
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+    }
     return KCMG_OK;
   });
 }

@@ -138,7 +138,53 @@ void launch_grad_lognu(int np, int dim, const int* n, const double* nu, const do
                        const double* F, const double* B, const double* lam, const double* u,
                        double* g, cudaStream_t s);
 
+// ---------------------------------------------------------------- coarse cycle kernel
+constexpr int kCoarseMaxCols = 128;   // basis capacity + 1 on the coarse levels
+
+struct CoarseLevel {
+  const void* A;        // row-interleaved FP64 operator (residual minimisation)
+  const void* As;       // row-interleaved operator of the smoother (its precision)
+  const void* Dinv;     // row-interleaved block inverses (smoother precision or BF16)
+  void *s0, *s1;        // smoother scratch vectors (smoother precision)
+  const int* nbr;
+  int n[3];
+  int N, G, rows_pad;
+  void *x, *r, *b, *z, *t, *w, *wre, *W, *Z;
+  int lcap, maxit;
+  double rtol;
+  LevelState* st;       // iteration/restart counters for the report
+};
+
+struct CoarseArgs {
+  CoarseLevel lv[KCMG_MAX_LEVELS];
+  int lev0, nlev, dim, np;
+  const void* P;               // prolongation matrices (FP64)
+  const double* Ainv;          // dense inverse of the coarsest operator
+  int Nc;
+  double omega;
+  int sweeps, lmax;
+  double brk;                  // breakdown threshold of Alg. 1
+  double* partial;             // 2 buffers of partial_stride doubles
+  size_t partial_stride;       // grid * kCoarseMaxCols
+  double* red;                 // kCoarseMaxCols reduced sums
+  unsigned int* bar_count;
+  unsigned int* bar_gen;
+  int* err;                    // set when a grid barrier timed out
+  // measurement: launches, device nanoseconds and algorithmic bytes of every launch
+  unsigned long long* stat_ns;
+  unsigned long long* stat_launches;
+  double* stat_bytes;
+  unsigned long long* stat_level_ns;   // [KCMG_MAX_LEVELS] time spent on each level
+  int smoother_bytes;          // bytes per element of the smoother operator
+  int inverse_bytes;           // bytes per element of the stored block inverses
+};
+
+template <typename T, typename TI>
+cudaError_t coarse_cycle_grid(int np, int dim, int threads, int* grid);
+template <typename T, typename TI>
+cudaError_t launch_coarse_cycle(const CoarseArgs& a, int grid, int threads, cudaStream_t s);
+
 int block_rows_for(int np);  // threads per block of the operator kernels (whole cells)
-bool np_supported(int np);
+bool np_supported(int np, int dim);
 
 }  // namespace kcmg

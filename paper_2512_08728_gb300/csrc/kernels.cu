@@ -831,7 +831,10 @@ __global__ void k_grad_lognu(int dim, Dims n, const double* __restrict__ nu, con
 }
 
 // ------------------------------------------------------------------ launchers
-bool np_supported(int np) { return np == 3 || np == 4 || np == 6 || np == 10 || np == 20; }
+// total-degree DG spaces: 2-D p = 1, 2, 3 (3, 6, 10 modes); 3-D p = 1, 2, 3 (4, 10, 20)
+bool np_supported(int np, int dim) {
+  return dim == 2 ? (np == 3 || np == 6 || np == 10) : dim == 3 ? (np == 4 || np == 10 || np == 20) : false;
+}
 
 int block_rows_for(int np) {
   switch (np) {
@@ -852,14 +855,25 @@ static inline int nblocks(size_t n, int t, int cap = 4096) {
 
 static Dims mkdims(const int* n) { Dims d; d.n[0] = n[0]; d.n[1] = n[1]; d.n[2] = n[2]; return d; }
 
-#define KCMG_NP_SWITCH(np, ...)                       \
-  switch (np) {                                       \
-    case 3: { constexpr int NP = 3; __VA_ARGS__; } break;   \
-    case 4: { constexpr int NP = 4; __VA_ARGS__; } break;   \
-    case 6: { constexpr int NP = 6; __VA_ARGS__; } break;   \
-    case 10: { constexpr int NP = 10; __VA_ARGS__; } break; \
-    case 20: { constexpr int NP = 20; __VA_ARGS__; } break; \
-    default: break;                                   \
+// dispatch over the supported (np, dim) pairs; the body sees NP, DIM and S = 2 DIM + 1
+#define KCMG_ND_SWITCH(np, dim, ...)                                                      \
+  switch (np * 10 + dim) {                                                                \
+    case 32: { constexpr int NP = 3, DIM = 2, S = 5; (void)S; __VA_ARGS__; } break;       \
+    case 62: { constexpr int NP = 6, DIM = 2, S = 5; (void)S; __VA_ARGS__; } break;       \
+    case 102: { constexpr int NP = 10, DIM = 2, S = 5; (void)S; __VA_ARGS__; } break;     \
+    case 43: { constexpr int NP = 4, DIM = 3, S = 7; (void)S; __VA_ARGS__; } break;       \
+    case 103: { constexpr int NP = 10, DIM = 3, S = 7; (void)S; __VA_ARGS__; } break;     \
+    case 203: { constexpr int NP = 20, DIM = 3, S = 7; (void)S; __VA_ARGS__; } break;     \
+    default: break;                                                                       \
+  }
+#define KCMG_NP_SWITCH(np, ...)                               \
+  switch (np) {                                               \
+    case 3: { constexpr int NP = 3; __VA_ARGS__; } break;     \
+    case 4: { constexpr int NP = 4; __VA_ARGS__; } break;     \
+    case 6: { constexpr int NP = 6; __VA_ARGS__; } break;     \
+    case 10: { constexpr int NP = 10; __VA_ARGS__; } break;   \
+    case 20: { constexpr int NP = 20; __VA_ARGS__; } break;   \
+    default: break;                                           \
   }
 
 template <typename T>
@@ -868,18 +882,11 @@ void launch_spmv(int np, int dim, const T* A, const int* nbr, int N, int G, int 
                  const EpiArgs& e, int conditional, cudaStream_t s) {
   const int grid = rows_pad / block_rows;
   const bool resid = b != nullptr, norm = e.kind != EPI_NONE;
-  KCMG_NP_SWITCH(np, {
-    if (dim == 2) {
-      if (resid && norm) k_spmv<T, NP, 5, true, true><<<grid, block_rows, 0, s>>>(A, nbr, N, G, x, y, b, partial, e, conditional);
-      else if (resid) k_spmv<T, NP, 5, true, false><<<grid, block_rows, 0, s>>>(A, nbr, N, G, x, y, b, partial, e, conditional);
-      else if (norm) k_spmv<T, NP, 5, false, true><<<grid, block_rows, 0, s>>>(A, nbr, N, G, x, y, b, partial, e, conditional);
-      else k_spmv<T, NP, 5, false, false><<<grid, block_rows, 0, s>>>(A, nbr, N, G, x, y, b, partial, e, conditional);
-    } else {
-      if (resid && norm) k_spmv<T, NP, 7, true, true><<<grid, block_rows, 0, s>>>(A, nbr, N, G, x, y, b, partial, e, conditional);
-      else if (resid) k_spmv<T, NP, 7, true, false><<<grid, block_rows, 0, s>>>(A, nbr, N, G, x, y, b, partial, e, conditional);
-      else if (norm) k_spmv<T, NP, 7, false, true><<<grid, block_rows, 0, s>>>(A, nbr, N, G, x, y, b, partial, e, conditional);
-      else k_spmv<T, NP, 7, false, false><<<grid, block_rows, 0, s>>>(A, nbr, N, G, x, y, b, partial, e, conditional);
-    }
+  KCMG_ND_SWITCH(np, dim, {
+    if (resid && norm) k_spmv<T, NP, S, true, true><<<grid, block_rows, 0, s>>>(A, nbr, N, G, x, y, b, partial, e, conditional);
+    else if (resid) k_spmv<T, NP, S, true, false><<<grid, block_rows, 0, s>>>(A, nbr, N, G, x, y, b, partial, e, conditional);
+    else if (norm) k_spmv<T, NP, S, false, true><<<grid, block_rows, 0, s>>>(A, nbr, N, G, x, y, b, partial, e, conditional);
+    else k_spmv<T, NP, S, false, false><<<grid, block_rows, 0, s>>>(A, nbr, N, G, x, y, b, partial, e, conditional);
   });
 }
 
@@ -889,14 +896,9 @@ void launch_bj_sweep(int np, int dim, const T* A, const TI* Dinv, const int* nbr
                      double omega, int first, cudaStream_t s) {
   const int grid = rows_pad / block_rows;
   const size_t sm = (size_t)block_rows * sizeof(T);
-  KCMG_NP_SWITCH(np, {
-    if (dim == 2) {
-      if (first) k_bj_sweep<T, TI, NP, 5, true><<<grid, block_rows, sm, s>>>(A, Dinv, nbr, N, G, r, zold, znew, omega);
-      else k_bj_sweep<T, TI, NP, 5, false><<<grid, block_rows, sm, s>>>(A, Dinv, nbr, N, G, r, zold, znew, omega);
-    } else {
-      if (first) k_bj_sweep<T, TI, NP, 7, true><<<grid, block_rows, sm, s>>>(A, Dinv, nbr, N, G, r, zold, znew, omega);
-      else k_bj_sweep<T, TI, NP, 7, false><<<grid, block_rows, sm, s>>>(A, Dinv, nbr, N, G, r, zold, znew, omega);
-    }
+  KCMG_ND_SWITCH(np, dim, {
+    if (first) k_bj_sweep<T, TI, NP, S, true><<<grid, block_rows, sm, s>>>(A, Dinv, nbr, N, G, r, zold, znew, omega);
+    else k_bj_sweep<T, TI, NP, S, false><<<grid, block_rows, sm, s>>>(A, Dinv, nbr, N, G, r, zold, znew, omega);
   });
 }
 
@@ -905,9 +907,8 @@ void launch_restrict(int np, int dim, const int* nf, const int* nc, const T* P, 
                      T* b, T* r, T* x, double* partial, const EpiArgs& e, cudaStream_t s) {
   const int Nc = nc[0] * nc[1] * (dim == 3 ? nc[2] : 1) * np;
   const int grid = nblocks(Nc, 256, 1 << 30);
-  KCMG_NP_SWITCH(np, {
-    if (dim == 2) k_restrict<T, TIN, NP, 2><<<grid, 256, 0, s>>>(mkdims(nf), mkdims(nc), P, rf, b, r, x, Nc, partial, e);
-    else k_restrict<T, TIN, NP, 3><<<grid, 256, 0, s>>>(mkdims(nf), mkdims(nc), P, rf, b, r, x, Nc, partial, e);
+  KCMG_ND_SWITCH(np, dim, {
+    k_restrict<T, TIN, NP, DIM><<<grid, 256, 0, s>>>(mkdims(nf), mkdims(nc), P, rf, b, r, x, Nc, partial, e);
   });
 }
 
@@ -916,9 +917,8 @@ void launch_prolong(int np, int dim, const int* nf, const int* nc, const T* P, c
                     TOUT* zf, cudaStream_t s) {
   const int Nf = nf[0] * nf[1] * (dim == 3 ? nf[2] : 1) * np;
   const int grid = nblocks(Nf, 256, 1 << 30);
-  KCMG_NP_SWITCH(np, {
-    if (dim == 2) k_prolong<T, TOUT, NP, 2><<<grid, 256, 0, s>>>(mkdims(nf), mkdims(nc), P, zc, zf, Nf);
-    else k_prolong<T, TOUT, NP, 3><<<grid, 256, 0, s>>>(mkdims(nf), mkdims(nc), P, zc, zf, Nf);
+  KCMG_ND_SWITCH(np, dim, {
+    k_prolong<T, TOUT, NP, DIM><<<grid, 256, 0, s>>>(mkdims(nf), mkdims(nc), P, zc, zf, Nf);
   });
 }
 
@@ -977,10 +977,9 @@ int launch_galerkin(int np, int dim, const double* Af, const int* nbrf, const in
   dim3 grid(Cc, 2 * dim + 1);
   const int threads = ((np * np + 31) / 32) * 32;
   int ok = 0;
-  KCMG_NP_SWITCH(np, {
+  KCMG_ND_SWITCH(np, dim, {
     ok = 1;
-    if (dim == 2) k_galerkin<NP, 2><<<grid, threads, 0, s>>>(Af, nbrf, mkdims(nf), mkdims(nc), P, Ac);
-    else k_galerkin<NP, 3><<<grid, threads, 0, s>>>(Af, nbrf, mkdims(nf), mkdims(nc), P, Ac);
+    k_galerkin<NP, DIM><<<grid, threads, 0, s>>>(Af, nbrf, mkdims(nf), mkdims(nc), P, Ac);
   });
   return ok;
 }

@@ -26,13 +26,14 @@ class kcmg_params(C.Structure):
                 ("blocks", C.c_void_p), ("prolong", C.c_void_p), ("omega", C.c_double),
                 ("sweeps", C.c_int), ("lvl_rtol", C.c_double * KCMG_MAX_LEVELS),
                 ("lvl_maxit", C.c_int * KCMG_MAX_LEVELS), ("lmax", C.c_int),
-                ("precision", C.c_int), ("use_graph", C.c_int)]
+                ("precision", C.c_int), ("use_graph", C.c_int), ("coarse_persistent", C.c_int)]
 
 
 class kcmg_info(C.Structure):
     _fields_ = [("iters", C.c_int), ("level_iters", C.c_int * KCMG_MAX_LEVELS),
                 ("restarts", C.c_int), ("refinements", C.c_int), ("res0", C.c_double),
-                ("rel_res", C.c_double), ("hist_cap", C.c_int), ("hist_len", C.c_int),
+                ("rel_res", C.c_double), ("kernel_launches", C.c_longlong),
+                ("hist_cap", C.c_int), ("hist_len", C.c_int),
                 ("hist", C.c_void_p), ("hist_type", C.c_void_p)]
 
 
@@ -68,6 +69,7 @@ def load_library():
         "kcmg_get_blocks": (ip, [vp, ip, vp]),
         "kcmg_rm_sequence": (ip, [vp, ip, vp, vp, vp, ip, vp, vp, C.POINTER(C.c_int)]),
         "kcmg_level_cells": (ip, [vp, ip]),
+        "kcmg_kernel_report": (ip, [vp, ip, vp, ip]),
         "kcmg_last_error": (C.c_char_p, [vp]),
         "kcmg_status_string": (C.c_char_p, [ip]),
         "kcmg_destroy": (None, [vp]),
@@ -85,6 +87,7 @@ def exported_symbols():
     return ["kcmg_default_params", "kcmg_setup", "kcmg_solve", "kcmg_solve_adjoint",
             "kcmg_grad_lognu", "kcmg_apply", "kcmg_smooth", "kcmg_restrict", "kcmg_prolong",
             "kcmg_coarse_solve", "kcmg_get_blocks", "kcmg_rm_sequence", "kcmg_level_cells",
+            "kcmg_kernel_report",
             "kcmg_last_error", "kcmg_status_string", "kcmg_destroy"]
 
 
@@ -172,7 +175,8 @@ def _info_dict(st, info, hist, htype):
     n = info.hist_len
     return {"status": st, "iters": info.iters, "level_iters": list(info.level_iters),
             "restarts": info.restarts, "refinements": info.refinements, "res0": info.res0,
-            "rel_res": info.rel_res, "hist": hist[:n].copy(), "hist_type": htype[:n].copy()}
+            "rel_res": info.rel_res, "kernel_launches": info.kernel_launches,
+            "hist": hist[:n].copy(), "hist_type": htype[:n].copy()}
 
 
 def kcmg_solve(ctx, b, x, rtol=1e-10, atol=0.0, maxiter=500, hist_cap=4096, adjoint=False):
@@ -193,6 +197,16 @@ def kcmg_solve_adjoint(ctx, g, lam, rtol=1e-10, atol=0.0, maxiter=500, hist_cap=
 
 def kcmg_level_cells(ctx, level):
     return load_library().kcmg_level_cells(ctx, level)
+
+
+def kcmg_kernel_report(ctx, reps=0):
+    """Coarse-cycle kernel counters since the last call and, with reps > 0, CUDA-event
+    timings of the level-0 operator application and smoother sweep (see kcmg.h)."""
+    out = np.zeros(7 + KCMG_MAX_LEVELS)
+    _check(ctx, load_library().kcmg_kernel_report(ctx, int(reps), out.ctypes.data, out.size))
+    return {"coarse_launches": int(out[0]), "coarse_ms": out[1], "coarse_bytes": out[2],
+            "spmv_ms": out[3], "spmv_bytes": out[4], "sweep_ms": out[5], "sweep_bytes": out[6],
+            "coarse_level_ms": out[7:].tolist()}
 
 
 def _unary(name, ctx, level, x, nout, *extra):
@@ -260,7 +274,7 @@ class KCycleSolver:
     """Owns one kcmg context built from a workloads.Problem-like object."""
 
     def __init__(self, problem, precision="fp64", use_graph=True, omega=0.7, sweeps=5,
-                 lmax=0, lvl_rtol=None, lvl_maxit=None, stream=None):
+                 lmax=0, lvl_rtol=None, lvl_maxit=None, coarse_persistent=True, stream=None):
         pr = problem
         self.dim, self.np_, self.nlevels = pr.d, pr.np_, pr.nlevels
         self.ndof = pr.ndof
@@ -268,6 +282,7 @@ class KCycleSolver:
         p.omega, p.sweeps, p.lmax = omega, sweeps, lmax
         p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         p.use_graph = int(use_graph)
+        p.coarse_persistent = int(coarse_persistent)
         if lvl_rtol is not None:
             for i, v in enumerate(lvl_rtol):
                 p.lvl_rtol[i] = v
@@ -315,6 +330,9 @@ class KCycleSolver:
 
     def rm_sequence(self, level, b, x0, zs):
         return kcmg_rm_sequence(self.ctx, level, b, x0, zs, self.np_)
+
+    def kernel_report(self, reps=0):
+        return kcmg_kernel_report(self.ctx, reps)
 
     def grad_lognu(self, nu, ref, lam, u):
         return kcmg_grad_lognu(self.ctx, nu, ref["V"], ref["F"], ref["B"], lam, u)

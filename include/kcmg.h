@@ -168,6 +168,25 @@ kcmg_status kcmg_rm_sequence(kcmg_ctx *ctx, int level, const double *b, const do
    nout >= 7. */
 kcmg_status kcmg_kernel_report(kcmg_ctx *ctx, int reps, double *out, int nout);
 
+/* r = b - A x with the finest-level FP64 operator, and *rnorm = ||r|| (a host double),
+   for callers that must not allocate device memory: for example host code inside a
+   stream capture, real-time loops that may not block on the driver's allocator, or
+   processes whose device memory pool a framework owns.  The paper has no counterpart;
+   this is a service of the library.
+   b, x, r: device pointers of length N (anything else returns KCMG_INVALID_ARG).
+   The call allocates nothing: its reduction scratch is a static device array of 257 KB,
+   present on every GPU that loads the library until the process exits.  It handles up to
+   32768 thread blocks (up to 10,485,760 rows at np = 10 or 20, 9,437,184 at np = 3 or 6,
+   8,388,608 at np = 4); larger problems return KCMG_INVALID_ARG.  The first call on a
+   device looks up the scratch's address there (cudaGetSymbolAddress, with that device
+   current); make that first call before any stream capture.  All calls share the scratch
+   and it keeps the last call's contents (the reduction counter is cleared at every call):
+   calls that overlap on the GPU (other streams, other host threads, other contexts on the
+   same device) race and must not be issued.  Stream-ordered on the context's stream;
+   returns after *rnorm is written. */
+kcmg_status kcmg_residual_noalloc(kcmg_ctx *ctx, const double *b, const double *x, double *r,
+                                  double *rnorm);
+
 /* Level sizes: number of cells of a level (0 if out of range). */
 int kcmg_level_cells(const kcmg_ctx *ctx, int level);
 

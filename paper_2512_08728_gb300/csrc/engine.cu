@@ -1147,6 +1147,27 @@ kcmg_status kcmg_kernel_report(kcmg_ctx* ctx, int reps, double* out, int nout) {
   });
 }
 
+kcmg_status kcmg_residual_noalloc(kcmg_ctx* ctx, const double* b, const double* x, double* r,
+                                  double* rnorm) {
+  return guarded(ctx, [&]() -> kcmg_status {
+    REQUIRE(b && x && r && rnorm, "null argument");
+    for (const void* p : {(const void*)b, (const void*)x, (const void*)r}) {
+      cudaPointerAttributes at;
+      const bool dev = cudaPointerGetAttributes(&at, p) == cudaSuccess &&
+                       (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
+      cudaGetLastError();
+      REQUIRE(dev, "kcmg_residual_noalloc: b, x and r must be device memory");
+    }
+    const Level& L = ctx->lv[0];
+    Level0View v{L.A64, L.nbr, L.N, L.G, L.rows_pad, L.block_rows, ctx->np, ctx->dim, ctx->s};
+    int too_large = 0;
+    CK(residual_noalloc(v, b, x, r, rnorm, &too_large));
+    REQUIRE(!too_large, "kcmg_residual_noalloc: %d rows need more than the 32768 thread blocks "
+            "its static scratch holds", L.N);
+    return KCMG_OK;
+  });
+}
+
 kcmg_status kcmg_grad_lognu(kcmg_ctx* ctx, const double* nu, const double* V, const double* F,
                             const double* B, const double* lambda, const double* u, double* g) {
   return guarded(ctx, [&]() -> kcmg_status {

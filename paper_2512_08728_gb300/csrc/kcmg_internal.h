@@ -184,6 +184,16 @@ cudaError_t coarse_cycle_grid(int np, int dim, int threads, int* grid);
 template <typename T, typename TI>
 cudaError_t launch_coarse_cycle(const CoarseArgs& a, int grid, int threads, cudaStream_t s);
 
+// finest-level FP64 operator of a context, for the no-allocation residual (noalloc.cu)
+struct Level0View {
+  const double* A;
+  const int* nbr;
+  int N, G, rows_pad, block_rows, np, dim;
+  cudaStream_t stream;
+};
+cudaError_t residual_noalloc(const Level0View& v, const double* b, const double* x, double* r,
+                             double* rnorm_host, int* too_large);
+
 int block_rows_for(int np);  // threads per block of the operator kernels (whole cells)
 bool np_supported(int np, int dim);
 

@@ -70,6 +70,7 @@ def load_library():
         "kcmg_rm_sequence": (ip, [vp, ip, vp, vp, vp, ip, vp, vp, C.POINTER(C.c_int)]),
         "kcmg_level_cells": (ip, [vp, ip]),
         "kcmg_kernel_report": (ip, [vp, ip, vp, ip]),
+        "kcmg_residual_noalloc": (ip, [vp, vp, vp, vp, C.POINTER(C.c_double)]),
         "kcmg_last_error": (C.c_char_p, [vp]),
         "kcmg_status_string": (C.c_char_p, [ip]),
         "kcmg_destroy": (None, [vp]),
@@ -87,7 +88,7 @@ def exported_symbols():
     return ["kcmg_default_params", "kcmg_setup", "kcmg_solve", "kcmg_solve_adjoint",
             "kcmg_grad_lognu", "kcmg_apply", "kcmg_smooth", "kcmg_restrict", "kcmg_prolong",
             "kcmg_coarse_solve", "kcmg_get_blocks", "kcmg_rm_sequence", "kcmg_level_cells",
-            "kcmg_kernel_report",
+            "kcmg_kernel_report", "kcmg_residual_noalloc",
             "kcmg_last_error", "kcmg_status_string", "kcmg_destroy"]
 
 
@@ -197,6 +198,18 @@ def kcmg_solve_adjoint(ctx, g, lam, rtol=1e-10, atol=0.0, maxiter=500, hist_cap=
 
 def kcmg_level_cells(ctx, level):
     return load_library().kcmg_level_cells(ctx, level)
+
+
+def kcmg_residual_noalloc(ctx, b, x, r):
+    """r = b - A x (finest-level FP64 operator) without any device allocation; b, x, r are
+    device tensors.  Returns ||r||.  See kcmg.h for the scratch it shares across calls."""
+    for a in (b, x, r):
+        if not (_is_torch(a) and a.is_cuda and a.dtype.is_floating_point and a.element_size() == 8):
+            raise ValueError("kcmg_residual_noalloc takes float64 CUDA tensors")
+    nrm = C.c_double(0.0)
+    _check(ctx, load_library().kcmg_residual_noalloc(ctx, _ptr(b)[0], _ptr(x)[0],
+                                                     _ptr(r, write=True)[0], C.byref(nrm)))
+    return nrm.value
 
 
 def kcmg_kernel_report(ctx, reps=0):

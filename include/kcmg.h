@@ -50,12 +50,13 @@ typedef enum {
 
 typedef enum {
     KCMG_FP64 = 0,         /* every kernel in FP64 */
-    KCMG_MIXED = 1,        /* smoother sweeps, transfers and every coarse level (operators,
-                              basis W/Z, residual minimisation) in FP32; level 0's residual
-                              minimisation (w = A z with the FP64 operator, W, Z, x, r), all
-                              Gram coefficients and the coarsest solve in FP64.  The FP64
-                              minimisation over FP32-computed corrections is the iterative
-                              refinement: the attainable residual is FP64's */
+    KCMG_MIXED = 1,        /* block-Jacobi sweeps in FP32 (FP32 operator blocks and
+                              inverses, FP32 intermediate iterates) on every level; the
+                              residual minimisation (w = A z with the FP64 operator, W, Z,
+                              x, r, Gram coefficients), the transfers and the coarsest solve
+                              in FP64.  The FP64 minimisation over FP32-computed corrections
+                              is the iterative refinement: the attainable residual is
+                              FP64's */
     KCMG_MIXED_BF16INV = 2 /* as KCMG_MIXED with the block-Jacobi inverses stored in BF16 */
 } kcmg_precision;
 
@@ -86,6 +87,11 @@ typedef struct {
     int coarse_persistent;   /* 1: every level below the finest runs in one persistent
                                 cooperative kernel per finest-level cycle; 0: one kernel
                                 per step (nested loops as conditional graph nodes) */
+    int tc_tf32_only;        /* batched solves (nrhs > 1) in the mixed forms: 0 (default) =
+                                every block product of the tensor-core sweeps is split into
+                                three TF32 products (head*head + head*tail + tail*head,
+                                FP32-level accuracy); 1 = a single TF32 product (about 2^-11
+                                relative per product; can stall the coarse levels) */
 } kcmg_params;
 
 /* Fill p with the defaults of Sec. 4.2 / Alg. BJ for the given sizes (blocks, prolong
@@ -118,7 +124,20 @@ typedef struct {
 kcmg_status kcmg_setup(kcmg_ctx **out, const kcmg_params *p, void *cuda_stream);
 
 /* Solve A x = b (Alg. 2 at level 0) until ||b - A x|| <= max(rtol ||b - A x0||, atol)
-   or maxiter level-0 cycles.  x: in x0, out x.  nrhs must be 1. info may be NULL. */
+   or maxiter level-0 cycles.  x: in x0, out x.  info may be NULL.
+   nrhs in [1, 32].  With nrhs > 1, b and x are [N][nrhs] (right-hand sides fastest) and
+   the columns are solved together: every column runs its own K-cycle (its own bases,
+   Gram coefficients and level criteria, Alg. 2 / Alg. 1 per column) while all columns
+   share each operator application.  A level's loop runs while any column is active on
+   it; a column that is not has its corrections discarded (masked).  Each column stops at
+   ||b_j - A x_j|| <= max(rtol ||b_j - A x0_j||, atol), confirmed by a compensated FP64
+   true residual.  The batched form is host-driven (use_graph is ignored).  Its level-0
+   basis holds lmax vectors per column (default 60 when lmax = 0), shrunk to what the
+   device can hold.  In the mixed forms the block-Jacobi sweeps run on the tensor cores
+   (TF32 products, FP32 accumulation), with launch shapes chosen by an autotuner at the
+   first batched solve (see kcmg_mrhs_tuning).  info: iters and level_iters count the
+   shared loop; rel_res is the largest relative residual over the columns and res0 the
+   largest initial residual; no history is recorded. */
 kcmg_status kcmg_solve(kcmg_ctx *ctx, const double *b, double *x, int nrhs, double rtol,
                        double atol, int maxiter, kcmg_info *info);
 
@@ -144,7 +163,7 @@ kcmg_status kcmg_grad_lognu(kcmg_ctx *ctx, const double *nu, const double *V, co
 kcmg_status kcmg_apply(kcmg_ctx *ctx, int level, int op, const double *x, double *y);
 /* z = BJ_level(r) from z = 0 (Alg. BJ, omega and sweeps of setup), inner precision. */
 kcmg_status kcmg_smooth(kcmg_ctx *ctx, int level, const double *r, double *z);
-/* rc = P^T r (level -> level+1) and z = P zc (level+1 -> level), inner precision. */
+/* rc = P^T r (level -> level+1) and z = P zc (level+1 -> level), FP64 in every form. */
 kcmg_status kcmg_restrict(kcmg_ctx *ctx, int level, const double *r, double *rc);
 kcmg_status kcmg_prolong(kcmg_ctx *ctx, int level, const double *zc, double *z);
 /* z = A_coarsest^{-1} r (FP64). */
@@ -186,6 +205,20 @@ kcmg_status kcmg_kernel_report(kcmg_ctx *ctx, int reps, double *out, int nout);
    returns after *rnorm is written. */
 kcmg_status kcmg_residual_noalloc(kcmg_ctx *ctx, const double *b, const double *x, double *r,
                                   double *rnorm);
+
+/* Batched component calls (right-hand sides fastest, [N_level][nrhs], nrhs in [2, 32],
+   level in [0, nlevels-2]); they run the kernels of the batched solve:
+   Y = A_level X with the FP64 operator, and Z = BJ_level(R) from Z = 0 (Alg. BJ, omega and
+   sweeps of setup) in the context's precision (mixed forms: tensor-core sweeps). */
+kcmg_status kcmg_apply_multi(kcmg_ctx *ctx, int level, int nrhs, const double *x, double *y);
+kcmg_status kcmg_smooth_multi(kcmg_ctx *ctx, int level, int nrhs, const double *r, double *z);
+
+/* Launch shapes the multi-right-hand-side autotuner chose at the first batched solve of
+   ctx: out[0] warps per block of the FP64 block SpMM, out[1] its time (ms), out[2] warps
+   per block of the tensor-core sweep, out[3] its grid (0 = one warp per cell), out[4] its
+   time (ms), out[5] level-0 basis capacity per column, out[6] nrhs, out[7] 1 if the
+   sweep splits each product into three TF32 products (tc_tf32_only = 0).  Zero-filled up to nout. */
+kcmg_status kcmg_mrhs_tuning(kcmg_ctx *ctx, double *out, int nout);
 
 /* Level sizes: number of cells of a level (0 if out of range). */
 int kcmg_level_cells(const kcmg_ctx *ctx, int level);

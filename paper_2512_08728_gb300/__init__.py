@@ -9,10 +9,12 @@ from .build import build
 from .kcmg import (KCycleSolver, KcmgError, kcmg_apply, kcmg_coarse_solve, kcmg_default_params,
                    kcmg_destroy, kcmg_get_blocks, kcmg_grad_lognu, kcmg_level_cells,
                    kcmg_prolong, kcmg_restrict, kcmg_rm_sequence, kcmg_setup, kcmg_smooth,
-                   kcmg_solve, kcmg_solve_adjoint, kcmg_residual_noalloc, load_library)
+                   kcmg_solve, kcmg_solve_adjoint, kcmg_residual_noalloc, kcmg_apply_multi,
+                   kcmg_smooth_multi, kcmg_mrhs_tuning, load_library)
 
 __all__ = ["build", "KCycleSolver", "KcmgError", "kcmg_apply", "kcmg_coarse_solve",
            "kcmg_default_params", "kcmg_destroy", "kcmg_get_blocks", "kcmg_grad_lognu",
            "kcmg_level_cells", "kcmg_prolong", "kcmg_restrict", "kcmg_rm_sequence",
            "kcmg_setup", "kcmg_smooth", "kcmg_solve", "kcmg_solve_adjoint",
-           "kcmg_residual_noalloc", "load_library"]
+           "kcmg_residual_noalloc", "kcmg_apply_multi", "kcmg_smooth_multi",
+           "kcmg_mrhs_tuning", "load_library"]

@@ -12,6 +12,8 @@
 #pragma once
 #include "kcmg_internal.h"
 
+#include <cuda/atomic>
+
 #include <cmath>
 
 namespace kcmg {
@@ -60,43 +62,67 @@ __device__ __forceinline__ double bsum(double v, double* sh) {
   return r;  // valid in thread 0
 }
 
+// NC block sums at once (one shared-memory exchange): results valid in thread 0.
+// sh: >= 32 * NC doubles.
+template <int NC>
+__device__ __forceinline__ void bsum_n(double (&v)[NC], double* sh) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
+  const int w = threadIdx.x >> 5, ln = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (ln == 0)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) sh[c * 32 + w] = v[c];
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      double r = (ln < nw) ? sh[c * 32 + ln] : 0.0;
+#pragma unroll
+      for (int o = 16; o; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+      v[c] = r;
+    }
+  }
+}
+
 template <typename T> __device__ __forceinline__ T ldv(const T* p) { return __ldcg(p); }
 
 }  // namespace
 
-// Grid barrier with a bounded wait.  Returns false (in every thread of the block) once
-// the error flag is set; callers then leave the kernel.
-static __device__ __forceinline__ bool cc_barrier(const CoarseArgs& a) {
+// Grid barrier with a bounded wait.  Every block adds one to a counter (acquire-release,
+// which publishes the block's writes) and waits until the counter reaches the total for
+// this generation; the host zeroes the counter before every launch.  gen: this block's
+// barrier count so far.  Returns false (in every thread of the block) once the error flag
+// is set; callers then leave the kernel.
+static __device__ __forceinline__ bool cc_barrier(const CoarseArgs& a, unsigned int& gen) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned int* gen = a.bar_gen;
-    volatile int* err = a.err;
-    int ok = (*err == 0);
+    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> cnt(*a.bar_count);
+    cuda::atomic_ref<int, cuda::thread_scope_device> err(*a.err);
+    int ok = err.load(cuda::memory_order_relaxed) == 0;
     if (ok) {
-      const unsigned int g = *gen;
-      __threadfence();
-      const unsigned int arrived = atomicAdd(a.bar_count, 1u);
-      if (arrived == gridDim.x - 1) {
-        atomicExch(a.bar_count, 0u);
-        __threadfence();
-        atomicAdd(a.bar_gen, 1u);
-      } else {
+      const unsigned int target = (gen + 1) * gridDim.x;
+      const unsigned int old = cnt.fetch_add(1u, cuda::memory_order_acq_rel);
+      if (old + 1 != target) {
         long long spins = 0;
-        while (*gen == g) {
-          if (*err) break;
-          if (++spins > (1LL << 22)) {   // ~1-3 s: far beyond any legitimate wait
-            atomicExch(a.err, 1);
-            break;
+        while (cnt.load(cuda::memory_order_acquire) < target) {
+          if ((++spins & 1023) == 0) {
+            if (err.load(cuda::memory_order_relaxed)) break;
+            if (spins > (1LL << 23)) {   // seconds: far beyond any legitimate wait
+              err.store(1, cuda::memory_order_relaxed);
+              break;
+            }
           }
-          __nanosleep(32);
         }
       }
-      __threadfence();
-      ok = (*err == 0);
+      ok = err.load(cuda::memory_order_relaxed) == 0;
     }
     s_ok = ok;
   }
+  ++gen;
   __syncthreads();
   return s_ok != 0;
 }
@@ -128,7 +154,9 @@ struct CoarseCycle {
   T* Ps;           // NCH*NP*NP (prolongation matrices)
   double* cw;      // coefficient vectors in shared memory: 2 * kCoarseMaxCols
   int rcount = 0;  // reductions done (selects the partial buffer)
+  unsigned int gen = 0;  // grid barriers passed (identical in every block)
   bool ok = true;
+  __device__ bool bar() { return cc_barrier(a, gen); }
   double bytes = 0.0;  // algorithmic bytes of this launch (kept by thread 0 of block 0)
 
   __device__ void count(double b) {
@@ -148,19 +176,24 @@ struct CoarseCycle {
   __device__ bool reduce_few(const double (&v)[NC]) {
     double* part = a.partial + (size_t)(rcount & 1) * a.partial_stride;
     rcount++;
+    double t[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      const double s = bsum(v[c], sh);
-      if (threadIdx.x == 0) part[(size_t)blockIdx.x * NC + c] = s;
-    }
-    if (!cc_barrier(a)) return false;
+    for (int c = 0; c < NC; ++c) t[c] = v[c];
+    bsum_n<NC>(t, sh);
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) part[(size_t)blockIdx.x * NC + c] = t[c];
+    if (!bar()) return false;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       double s = 0.0;
       for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += __ldcg(part + (size_t)b * NC + c);
-      s = bsum(s, sh);
-      if (threadIdx.x == 0) red_s[c] = s;
+      t[c] = s;
     }
+    bsum_n<NC>(t, sh);
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) red_s[c] = t[c];
     __syncthreads();
     return true;
   }
@@ -168,14 +201,33 @@ struct CoarseCycle {
   // many columns: partial[b][c] already written by every block for c < nc; owners
   // reduce one column each, then all blocks read the totals into red_s
   __device__ bool reduce_cols(double* part, int nc) {
-    if (!cc_barrier(a)) return false;
+    if (nc * (int)gridDim.x <= 4096) {   // few columns: every block sums all of them
+      if (!bar()) return false;
+      for (int c0 = 0; c0 < nc; c0 += 8) {
+        double t[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          t[c] = 0.0;
+          if (c0 + c < nc)
+            for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t[c] += __ldcg(part + (size_t)b * nc + c0 + c);
+        }
+        bsum_n<8>(t, sh);
+        if (threadIdx.x == 0)
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            if (c0 + c < nc) red_s[c0 + c] = t[c];
+      }
+      __syncthreads();
+      return true;
+    }
+    if (!bar()) return false;
     for (int c = blockIdx.x; c < nc; c += gridDim.x) {
       double s = 0.0;
       for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += __ldcg(part + (size_t)b * nc + c);
       s = bsum(s, sh);
       if (threadIdx.x == 0) a.red[c] = s;
     }
-    if (!cc_barrier(a)) return false;
+    if (!bar()) return false;
     for (int c = threadIdx.x; c < nc; c += blockDim.x) red_s[c] = __ldcg(a.red + c);
     __syncthreads();
     return true;
@@ -280,7 +332,7 @@ struct CoarseCycle {
       const TS* zo = sb[(k + 1) & 1];
       if (k == a.sweeps - 1) sweep<T>(C, r, zo, out, k == 0);
       else sweep<TS>(C, r, zo, sb[k & 1], k == 0);
-      ok = cc_barrier(a);
+      ok = bar();
     }
     return out;
   }
@@ -321,7 +373,7 @@ struct CoarseCycle {
         for (int i = 0; i < l; ++i) s = fma((T)(-cw[i]), ldv(W + (size_t)i * N + j), s);
         wre[j] = s;
       }
-      if (!cc_barrier(a)) return false;
+      if (!bar()) return false;
       double* part2 = a.partial + (size_t)(rcount & 1) * a.partial_stride;
       rcount++;
       dots(W, N, wre, l, part2);
@@ -384,12 +436,20 @@ struct CoarseCycle {
       }
       r2 += (double)(rv * rv);
     }
-    count(discard ? (double)N * 8 : (double)N * 8 * 8);
-    {
+    count(discard ? 0.0 : (double)N * 8 * 8);
+    // ||r - alpha w||^2 = ||r||^2 - alpha^2 for unit w with alpha = w . r; reduce the
+    // updated vector explicitly only if that cancels more than four digits
+    const double r2old = sc.rnorm * sc.rnorm;
+    const double r2new = r2old - alp * alp;
+    if (discard) {
+      // x, r unchanged
+    } else if (r2new > 1e-4 * r2old) {
+      sc.rnorm = sqrt(r2new);
+    } else {
       double v[1] = {r2};
       if (!reduce_few<1>(v)) return false;
+      sc.rnorm = sqrt(red_s[0]);
     }
-    sc.rnorm = sqrt(red_s[0]);
     if (!discard) sc.l++;
     return true;
   }
@@ -412,11 +472,11 @@ struct CoarseCycle {
           acc[c] += (double)p;
         }
       }
+      bsum_n<8>(acc, sh);
+      if (threadIdx.x == 0)
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const double s = bsum(acc[c], sh);
-        if (threadIdx.x == 0 && c0 + c < nc) part[(size_t)blockIdx.x * nc + c0 + c] = s;
-      }
+        for (int c = 0; c < 8; ++c)
+          if (c0 + c < nc) part[(size_t)blockIdx.x * nc + c0 + c] = acc[c];
     }
   }
 
@@ -532,20 +592,21 @@ struct CoarseCycle {
           mark(lev);
           if (lev == lev0) break;
           --lev;                                                   // return to the caller
-          if (!(ok = cc_barrier(a))) break;
+          if (!(ok = bar())) break;
           continue;
         }
         ++guard[lev];
         T* z = smooth(lev, vec(C.r));                              // pre-smoother
         if (!ok || !(ok = rm(lev, z, s))) break;
+        if (!(ok = bar())) break;                                  // r complete everywhere
         const bool direct = (lev + 1 == a.nlev - 1);
         const double nb = restrict_(lev, !direct);                 // r_c = R r
         phase[lev] = AFTER_COARSE;
         if (direct) {
-          if (!(ok = cc_barrier(a))) break;
+          if (!(ok = bar())) break;
           mark(lev);
           coarse_solve(lev + 1);                                   // z_c = A_c \ r_c
-          if (!(ok = cc_barrier(a))) break;
+          if (!(ok = bar())) break;
           mark(lev + 1);
         } else {
           double v[1] = {nb};
@@ -560,13 +621,14 @@ struct CoarseCycle {
       }
       // AFTER_COARSE: prolongate, minimise, post-smooth, minimise
       prolong(lev);                                                // z = P z_c
-      if (!(ok = cc_barrier(a))) break;
+      if (!(ok = bar())) break;
       if (!(ok = rm(lev, vec(C.z), s))) break;
       T* z = smooth(lev, vec(C.r));                                // post-smoother
       if (!ok || !(ok = rm(lev, z, s))) break;
       s.it++;
       const int cap = (a.lmax > 0 && a.lmax < C.lcap) ? a.lmax : C.lcap;
       if (s.l + 3 > cap) {                                         // restart: r = b - A x
+        if (!(ok = bar())) break;
         double v[1] = {spmv(lev, vec(C.x), vec(C.r), vec(C.b))};
         if (!(ok = reduce_few<1>(v))) break;
         s.rnorm = sqrt(red_s[0]);
@@ -582,7 +644,7 @@ template <typename TS, typename TI, int NP, int DIM>
 __global__ void __launch_bounds__(320, 1) k_coarse_cycle(CoarseArgs a) {
   using T = double;
   extern __shared__ unsigned char smem_raw[];
-  __shared__ double sh[32];
+  __shared__ double sh[32 * 8];
   __shared__ double red_s[kCoarseMaxCols];
   __shared__ double cw[2 * kCoarseMaxCols];
   constexpr int NCH = 1 << DIM;
@@ -606,7 +668,7 @@ __global__ void __launch_bounds__(320, 1) k_coarse_cycle(CoarseArgs a) {
   cc.count((double)C.N * 8);
   cc.run(a.lev0);   // reads ||b||^2 from red_s[0]
   // device time of this launch: every block has passed the last barrier of the cycle
-  if (cc.ok) cc.ok = cc_barrier(a);
+  if (cc.ok) cc.ok = cc.bar();
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     unsigned long long t1;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));

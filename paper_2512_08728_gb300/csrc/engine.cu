@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <type_traits>
@@ -31,7 +32,8 @@ struct Level {
   // mixed forms: FP32 buffers of the smoother sweeps (the level's vectors are FP64)
   float *r_lo = nullptr, *z_lo = nullptr, *t_lo = nullptr;
   int lcap = 0;
-  int nblk = 1;                     // blocks of the vector / dot kernels
+  int nblk = 1;                     // blocks of the multi-column dot kernels
+  int nblk2 = 1;                    // blocks of the update / finish / norm kernels
   double *h = nullptr, *h2 = nullptr, *partial = nullptr;
   LevelState* st = nullptr;
 };
@@ -61,9 +63,11 @@ struct kcmg_ctx {
   bool graph_ready = false;
   // persistent coarse cycle (levels >= 1 in one cooperative launch per level-0 cycle)
   bool coarse_kernel = false;
+  int cc_lev0 = 0;   // first level run by the persistent kernel
   int cc_grid = 0;
   CoarseArgs cc{};
   long long graph_body_launches = 0;  // kernels per level-0 loop body of the graph
+  long long graph_body_kernels[KCMG_MAX_LEVELS] = {};
   long long last_launches = 0;        // kernels of the last cycle run
   // coarse-cycle counters (launches, ns, algorithmic bytes) and report scratch
   unsigned long long* stat_ns = nullptr;
@@ -71,6 +75,7 @@ struct kcmg_ctx {
   double* stat_bytes = nullptr;
   unsigned long long* stat_level_ns = nullptr;
   kcmg_ctx* adj = nullptr;       // transposed hierarchy (may be this)
+  MrhsEngine* mrhs = nullptr;    // batched multi-right-hand-side solver (built on demand)
   bool adj_built = false;
   std::vector<void*> allocs;
   std::string err;
@@ -139,6 +144,9 @@ void setup_level_geometry(kcmg_ctx* ctx, Level& L, int l) {
   L.nblk = (L.N + kVecThreads * 4 - 1) / (kVecThreads * 4);
   if (L.nblk > kDotBlocksMax) L.nblk = kDotBlocksMax;
   if (L.nblk < 1) L.nblk = 1;
+  L.nblk2 = (L.N + kVecThreads - 1) / kVecThreads;   // one element per thread
+  if (L.nblk2 > 2048) L.nblk2 = 2048;
+  if (L.nblk2 < 1) L.nblk2 = 1;
   L.nbr = dalloc<int>(ctx, (size_t)L.ncell * 2 * ctx->dim);
   launch_build_nbr(ctx->dim, L.n, L.nbr, ctx->s);
 }
@@ -243,11 +251,13 @@ void build_hierarchy(kcmg_ctx* ctx, const double* blocks_src) {
 // FP64 residual minimisation over FP32-smoothed corrections acts as the iterative
 // refinement (the attainable residual is FP64's).
 void launch_coarse(kcmg_ctx* ctx, cudaStream_t s) {
+  CK(cudaMemsetAsync(ctx->cc.bar_count, 0, sizeof(unsigned int), s));   // barrier counter
   cudaError_t err;
-  if (!ctx->mixed) err = launch_coarse_cycle<double, double>(ctx->cc, ctx->cc_grid, ctx->lv[1].block_rows, s);
+  const int thr = ctx->lv[ctx->cc_lev0].block_rows;
+  if (!ctx->mixed) err = launch_coarse_cycle<double, double>(ctx->cc, ctx->cc_grid, thr, s);
   else if (ctx->p.precision == KCMG_MIXED_BF16INV)
-    err = launch_coarse_cycle<float, __nv_bfloat16>(ctx->cc, ctx->cc_grid, ctx->lv[1].block_rows, s);
-  else err = launch_coarse_cycle<float, float>(ctx->cc, ctx->cc_grid, ctx->lv[1].block_rows, s);
+    err = launch_coarse_cycle<float, __nv_bfloat16>(ctx->cc, ctx->cc_grid, thr, s);
+  else err = launch_coarse_cycle<float, float>(ctx->cc, ctx->cc_grid, thr, s);
   CK(err);
 }
 
@@ -334,14 +344,14 @@ struct Cycle {
     launch_spmv<V>(ctx->np, ctx->dim, Aop, L.nbr, L.N, L.G, L.rows_pad, L.block_rows, z, w,
                    nullptr, L.partial, none, 0, s);
     launch_gram_dots<V>(W, L.N, w, L.lcap, L.nblk, L.partial, epi(lev, EPI_GRAM1), 0, s);
-    launch_gram_apply<V>(W, L.N, w, wre, L.lcap, L.nblk, L.st, L.h, s);
+    launch_gram_apply<V>(W, L.N, w, wre, L.lcap, L.nblk2, L.st, L.h, s);
     launch_gram_dots<V>(W, L.N, wre, L.lcap, L.nblk, L.partial, epi(lev, EPI_GRAM2), 1, s);
-    launch_gram_update<V>(W, Z, L.N, w, wre, z, static_cast<V*>(L.r), L.lcap, L.nblk, L.partial,
+    launch_gram_update<V>(W, Z, L.N, w, wre, z, static_cast<V*>(L.r), L.lcap, L.nblk2, L.partial,
                           epi(lev, EPI_UPDATE), s);
     EpiArgs fin = epi(lev, EPI_FINISH);
     fin.end_iter = end_iter;
     fin.hist_type = htype;
-    launch_rm_finish<V>(W, Z, L.N, static_cast<V*>(L.x), static_cast<V*>(L.r), L.nblk, L.partial,
+    launch_rm_finish<V>(W, Z, L.N, static_cast<V*>(L.x), static_cast<V*>(L.r), L.nblk2, L.partial,
                         fin, s);
   }
 
@@ -358,7 +368,7 @@ struct Cycle {
       launch_restrict<V, V>(ctx->np, ctx->dim, L.n, C.n, ctx->P64, static_cast<V*>(L.r),
                             static_cast<V*>(C.b), nullptr, nullptr, nullptr, EpiArgs{}, s);
       launch_coarse_gemv<V>(ctx->Ainv, ctx->Nc, static_cast<V*>(C.b), static_cast<V*>(C.x), s);
-    } else if (lev == 0 && ctx->coarse_kernel) {                           // levels >= 1 in
+    } else if (ctx->coarse_kernel && lev + 1 == ctx->cc_lev0) {            // small levels in
       launch_restrict<V, V>(ctx->np, ctx->dim, L.n, C.n, ctx->P64, static_cast<V*>(L.r),  // one
                             static_cast<V*>(C.b), static_cast<V*>(C.r), static_cast<V*>(C.x),  // launch
                             nullptr, EpiArgs{}, s);
@@ -386,12 +396,20 @@ struct Cycle {
     z = smooth<V>(lev, static_cast<V*>(L.r), s);                           // post-smoother
     rm<V>(lev, Aop, z, 1, 3, s);
     // restart check: r = b - A x on request, then the loop condition of this level
-    launch_spmv<V>(ctx->np, ctx->dim, Aop, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
-                   static_cast<V*>(L.x), static_cast<V*>(L.r), static_cast<V*>(L.b), L.partial,
-                   epi(lev, EPI_RESTART), 1, s);
+    // (compensated on level 0, where the tolerance can sit near the attainable accuracy)
+    if (lev == 0)
+      launch_residual_dd(ctx->np, ctx->dim, (const double*)Aop, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
+                         (const double*)L.x, (double*)L.r, (const double*)L.b, L.partial,
+                         epi(lev, EPI_RESTART), 1, s);
+    else
+      launch_spmv<V>(ctx->np, ctx->dim, Aop, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
+                     static_cast<V*>(L.x), static_cast<V*>(L.r), static_cast<V*>(L.b), L.partial,
+                     epi(lev, EPI_RESTART), 1, s);
   }
 
-  long long body_launches = 0;   // level-0 loop body (capture)
+  long long body_launches = 0;                        // level-0 loop body (capture)
+  long long body_kernels[KCMG_MAX_LEVELS] = {};       // kernels of one body per level,
+  long long loop_total[KCMG_MAX_LEVELS + 1] = {};     // excluding nested loops
 
   bool read_cond(int lev) {
     int c = 0;
@@ -426,7 +444,10 @@ struct Cycle {
     CK(cudaStreamBeginCaptureToGraph(bs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                      cudaStreamCaptureModeRelaxed));
     const long long before = launches;
+    loop_total[lev + 1] = 0;
     body<V>(lev, Aop, bs);
+    loop_total[lev] = launches - before;
+    body_kernels[lev] = loop_total[lev] - loop_total[lev + 1];
     if (lev == 0) body_launches = launches - before;
     CK(cudaStreamEndCapture(bs, nullptr));
   }
@@ -444,9 +465,9 @@ struct Cycle {
       CK(cudaStreamGetCaptureInfo(s, &cs, &id, &g, &deps, &ed, &nd));
       CK(cudaGraphConditionalHandleCreate(&handle[0], g, 0, 0));
     }
-    launch_spmv<T0>(ctx->np, ctx->dim, (const T0*)L.A64, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
-                    static_cast<T0*>(L.x), static_cast<T0*>(L.r), static_cast<T0*>(L.b), L.partial,
-                    epi(0, EPI_MG_BEGIN), 0, s);
+    launch_residual_dd(ctx->np, ctx->dim, L.A64, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
+                       static_cast<double*>(L.x), static_cast<double*>(L.r), static_cast<double*>(L.b),
+                       L.partial, epi(0, EPI_MG_BEGIN), 0, s);
     loop<T0>(0, (const T0*)L.A64, s);
   }
 };
@@ -503,8 +524,9 @@ void run_cycle(kcmg_ctx* ctx) {
         throw;
       }
       CK(cudaStreamEndCapture(ctx->s, &g));
-      // kernel launches per execution: exact when the levels below 0 run in one kernel
-      ctx->graph_body_launches = ctx->coarse_kernel ? cy.body_launches : -1;
+      // kernels per execution of each level's loop body (nested loops excluded)
+      ctx->graph_body_launches = 0;
+      for (int l = 0; l < KCMG_MAX_LEVELS; ++l) ctx->graph_body_kernels[l] = cy.body_kernels[l];
       CK(cudaGraphInstantiate(&ctx->gexec, g, 0));
       CK(cudaGraphDestroy(g));
       ctx->graph_ready = true;
@@ -527,8 +549,8 @@ double fp64_residual(kcmg_ctx* ctx, const double* x, const double* b, double* r)
   e.st = L.st;  // only its reduction ticket is used
   e.kind = EPI_NORM;
   e.out = ctx->scal;
-  launch_spmv<double>(ctx->np, ctx->dim, L.A64, L.nbr, L.N, L.G, L.rows_pad, L.block_rows, x, r, b,
-                      L.partial, e, 0, ctx->s);
+  launch_residual_dd(ctx->np, ctx->dim, L.A64, L.nbr, L.N, L.G, L.rows_pad, L.block_rows, x, r, b,
+                     L.partial, e, 0, ctx->s);
   CK(cudaGetLastError());
   double v = 0;
   CK(cudaMemcpyAsync(&v, ctx->scal, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
@@ -558,10 +580,11 @@ void fill_info(kcmg_ctx* ctx, kcmg_info* info, const StateReport& rep, double re
   info->refinements = ctx->mixed ? rep.st[0].nrestart + 1 : 0;
   info->res0 = res0;
   info->rel_res = rel;
-  if (ctx->last_launches == -2)   // graph: begin + cycles x body + final residual
-    info->kernel_launches = ctx->graph_body_launches < 0 ? -1
-                            : 2 + (long long)rep.st[0].guard * ctx->graph_body_launches;
-  else
+  if (ctx->last_launches == -2) {   // graph: begin + sum over levels of bodies x kernels
+    long long n = 2;                  // initial and final residual
+    for (int l = 0; l < ctx->nlev; ++l) n += (long long)rep.st[l].guard * ctx->graph_body_kernels[l];
+    info->kernel_launches = n;
+  } else
     info->kernel_launches = ctx->last_launches + 1;
   const int hl = rep.st[0].hist_len;
   info->hist_len = 0;
@@ -610,6 +633,43 @@ kcmg_status solve_impl(kcmg_ctx* ctx, const double* b, double* x, double rtol, d
 kcmg_ctx* build_ctx(const kcmg_params* p, cudaStream_t user, const double* blocks_override,
                     kcmg_status* out_status, std::string* msg);
 
+// the hierarchy of ctx as the batched solver sees it
+MrhsView mrhs_view(kcmg_ctx* ctx) {
+  MrhsView v;
+  memset(&v, 0, sizeof v);
+  v.dim = ctx->dim;
+  v.np = ctx->np;
+  v.nlev = ctx->nlev;
+  for (int l = 0; l < ctx->nlev; ++l) {
+    const Level& L = ctx->lv[l];
+    for (int j = 0; j < 3; ++j) v.n[l][j] = L.n[j];
+    v.ncell[l] = L.ncell;
+    v.N[l] = L.N;
+    v.nat[l] = L.nat;
+    v.nbr[l] = L.nbr;
+  }
+  v.P = ctx->P64;
+  v.Ainv = ctx->Ainv;
+  v.Nc = ctx->Nc;
+  v.omega = ctx->p.omega;
+  v.sweeps = ctx->p.sweeps;
+  for (int l = 0; l < KCMG_MAX_LEVELS; ++l) {
+    v.lvl_rtol[l] = ctx->p.lvl_rtol[l];
+    v.lvl_maxit[l] = ctx->p.lvl_maxit[l];
+  }
+  v.lmax = ctx->p.lmax;
+  v.precision = ctx->p.precision;
+  v.tc_tf32_only = ctx->p.tc_tf32_only;
+  v.s = ctx->s;
+  return v;
+}
+
+// batched solve of nrhs > 1 columns on the hierarchy of ctx
+kcmg_status solve_multi(kcmg_ctx* ctx, const double* b, double* x, int nrhs, double rtol, double atol,
+                        int maxiter, kcmg_info* info) {
+  return mrhs_solve(&ctx->mrhs, mrhs_view(ctx), b, x, nrhs, rtol, atol, maxiter, info, &ctx->err);
+}
+
 }  // namespace
 
 // ====================================================================== C interface
@@ -657,6 +717,7 @@ void kcmg_destroy(kcmg_ctx* ctx) {
   if (!ctx) return;
   if (ctx->adj && ctx->adj != ctx) kcmg_destroy(ctx->adj);
   if (ctx->s) cudaStreamSynchronize(ctx->s);
+  if (ctx->mrhs) mrhs_destroy(ctx->mrhs);
   if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
   for (void* p : ctx->allocs) cudaFree(p);
   if (ctx->stage_big) cudaFree(ctx->stage_big);
@@ -750,23 +811,37 @@ kcmg_ctx* build_ctx(const kcmg_params* p, cudaStream_t user, const double* block
       C.x = dalloc<double>(ctx, C.N);
     }
     // persistent coarse cycle for levels >= 1 (needs at least one iterated coarse level)
-    ctx->coarse_kernel = p->coarse_persistent && ctx->nlev > 2;
-    if (ctx->coarse_kernel) {
+    // The persistent kernel takes the coarse levels from the first one small enough that
+    // a kernel per step would be latency-bound (levels above stay on full-occupancy
+    // kernels under a nested conditional node); it needs at least one iterated level.
+    {
+      int rows_max = 100000;
+      if (const char* ev = getenv("KCMG_PERSISTENT_ROWS")) rows_max = atoi(ev);
+      ctx->cc_lev0 = 0;
       for (int l = 1; l < ctx->nlev - 1; ++l)
+        if (ctx->lv[l].N <= rows_max) { ctx->cc_lev0 = l; break; }
+    }
+    ctx->coarse_kernel = p->coarse_persistent && ctx->cc_lev0 > 0;
+    if (ctx->coarse_kernel) {
+      for (int l = ctx->cc_lev0; l < ctx->nlev - 1; ++l)
         REQUIRE(ctx->lv[l].lcap + 1 <= kCoarseMaxCols,
                 "level %d keeps %d basis vectors; the persistent coarse cycle supports %d",
                 l, ctx->lv[l].lcap, kCoarseMaxCols - 1);
       int grid = 0;
-      const int thr = ctx->lv[1].block_rows;
+      const int thr = ctx->lv[ctx->cc_lev0].block_rows;
       cudaError_t ge;
       if (!ctx->mixed) ge = coarse_cycle_grid<double, double>(ctx->np, ctx->dim, thr, &grid);
       else if (p->precision == KCMG_MIXED_BF16INV) ge = coarse_cycle_grid<float, __nv_bfloat16>(ctx->np, ctx->dim, thr, &grid);
       else ge = coarse_cycle_grid<float, float>(ctx->np, ctx->dim, thr, &grid);
       CK(ge);
+      if (const char* ev = getenv("KCMG_COARSE_GRID")) {   // tuning override, capped at residency
+        const int g = atoi(ev);
+        if (g > 0 && g < grid) grid = g;
+      }
       ctx->cc_grid = grid;
       CoarseArgs& a = ctx->cc;
       memset(&a, 0, sizeof a);
-      a.lev0 = 1;
+      a.lev0 = ctx->cc_lev0;
       a.nlev = ctx->nlev;
       a.dim = ctx->dim;
       a.np = ctx->np;
@@ -916,8 +991,9 @@ kcmg_status kcmg_solve(kcmg_ctx* ctx, const double* b, double* x, int nrhs, doub
                        double atol, int maxiter, kcmg_info* info) {
   return guarded(ctx, [&]() -> kcmg_status {
     REQUIRE(b && x, "b and x must be non-null");
-    REQUIRE(nrhs == 1, "nrhs must be 1");
+    REQUIRE(nrhs >= 1 && nrhs <= kMaxRhs, "nrhs must be in [1, %d]", kMaxRhs);
     REQUIRE(rtol >= 0 && atol >= 0 && maxiter >= 0, "negative tolerance or maxiter");
+    if (nrhs > 1) return solve_multi(ctx, b, x, nrhs, rtol, atol, maxiter, info);
     return solve_impl(ctx, b, x, rtol, atol, maxiter, info);
   });
 }
@@ -926,11 +1002,14 @@ kcmg_status kcmg_solve_adjoint(kcmg_ctx* ctx, const double* g, double* lambda, i
                                double rtol, double atol, int maxiter, kcmg_info* info) {
   return guarded(ctx, [&]() -> kcmg_status {
     REQUIRE(g && lambda, "g and lambda must be non-null");
-    REQUIRE(nrhs == 1, "nrhs must be 1");
+    REQUIRE(nrhs >= 1 && nrhs <= kMaxRhs, "nrhs must be in [1, %d]", kMaxRhs);
+    REQUIRE(rtol >= 0 && atol >= 0 && maxiter >= 0, "negative tolerance or maxiter");
     kcmg_status st = ensure_adjoint(ctx);
     if (st != KCMG_OK) return st;
-    if (ctx->adj == ctx) return solve_impl(ctx, g, lambda, rtol, atol, maxiter, info);
-    kcmg_status s2 = solve_impl(ctx->adj, g, lambda, rtol, atol, maxiter, info);
+    kcmg_ctx* a = ctx->adj;
+    kcmg_status s2 = nrhs > 1 ? solve_multi(a, g, lambda, nrhs, rtol, atol, maxiter, info)
+                              : solve_impl(a, g, lambda, rtol, atol, maxiter, info);
+    if (a == ctx) return s2;
     if (s2 != KCMG_OK && s2 != KCMG_NOT_CONVERGED) set_err(ctx, "%s", ctx->adj->err.c_str());
     return s2;
   });
@@ -1067,6 +1146,36 @@ kcmg_status kcmg_rm_sequence(kcmg_ctx* ctx, int level, const double* b, const do
     CK(cudaMemcpyAsync(&h, L.st, sizeof h, cudaMemcpyDeviceToHost, ctx->s));
     CK(cudaStreamSynchronize(ctx->s));
     *l = h.l;
+    return KCMG_OK;
+  });
+}
+
+kcmg_status kcmg_apply_multi(kcmg_ctx* ctx, int level, int nrhs, const double* x, double* y) {
+  return guarded(ctx, [&]() -> kcmg_status {
+    REQUIRE(level >= 0 && level < ctx->nlev - 1 && x && y, "bad level or null vector");
+    REQUIRE(nrhs >= 2 && nrhs <= kMaxRhs, "nrhs must be in [2, %d]", kMaxRhs);
+    kcmg_status st = mrhs_ensure(&ctx->mrhs, mrhs_view(ctx), nrhs, &ctx->err);
+    if (st != KCMG_OK) return st;
+    return mrhs_apply(ctx->mrhs, level, x, y);
+  });
+}
+
+kcmg_status kcmg_smooth_multi(kcmg_ctx* ctx, int level, int nrhs, const double* r, double* z) {
+  return guarded(ctx, [&]() -> kcmg_status {
+    REQUIRE(level >= 0 && level < ctx->nlev - 1 && r && z, "bad level or null vector");
+    REQUIRE(nrhs >= 2 && nrhs <= kMaxRhs, "nrhs must be in [2, %d]", kMaxRhs);
+    kcmg_status st = mrhs_ensure(&ctx->mrhs, mrhs_view(ctx), nrhs, &ctx->err);
+    if (st != KCMG_OK) return st;
+    return mrhs_smooth(ctx->mrhs, level, r, z);
+  });
+}
+
+kcmg_status kcmg_mrhs_tuning(kcmg_ctx* ctx, double* out, int nout) {
+  return guarded(ctx, [&]() -> kcmg_status {
+    REQUIRE(out && nout >= 1, "out must hold at least one value");
+    for (int i = 0; i < nout; ++i) out[i] = 0.0;
+    REQUIRE(ctx->mrhs, "no multi-right-hand-side solve has run on this context");
+    mrhs_tuning(ctx->mrhs, out, nout);
     return KCMG_OK;
   });
 }

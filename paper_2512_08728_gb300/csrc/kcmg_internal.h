@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 #include <cstddef>
 #include <cstdint>
+#include <string>
 
 #include "kcmg.h"
 
@@ -79,6 +80,10 @@ template <typename T>
 void launch_spmv(int np, int dim, const T* A, const int* nbr, int N, int G, int rows_pad,
                  int block_rows, const T* x, T* y, const T* b, double* partial,
                  const EpiArgs& e, int conditional, cudaStream_t s);
+// compensated (double-double accumulated) residual r = b - A x with ||r||^2 and epilogue
+void launch_residual_dd(int np, int dim, const double* A, const int* nbr, int N, int G, int rows_pad,
+                        int block_rows, const double* x, double* r, const double* b, double* partial,
+                        const EpiArgs& e, int conditional, cudaStream_t s);
 template <typename T, typename TI>
 void launch_bj_sweep(int np, int dim, const T* A, const TI* Dinv, const int* nbr, int N, int G,
                      int rows_pad, int block_rows, const T* r, const T* zold, T* znew,
@@ -193,6 +198,45 @@ struct Level0View {
 };
 cudaError_t residual_noalloc(const Level0View& v, const double* b, const double* x, double* r,
                              double* rnorm_host, int* too_large);
+
+// ---------------------------------------------------------------- multi-right-hand-side solve
+// Batched K-cycle over up to kMaxRhs right-hand sides (mrhs.cu).  Every right-hand side
+// keeps its own basis W, Z, coefficients and level criteria; all of them share each
+// operator application.  Vectors are [N][R] (right-hand sides fastest).
+constexpr int kMaxRhs = 32;
+
+struct MrhsView {               // the context's hierarchy, as the batched solve sees it
+  int dim, np, nlev;
+  int n[KCMG_MAX_LEVELS][3];
+  int ncell[KCMG_MAX_LEVELS], N[KCMG_MAX_LEVELS];
+  const double* nat[KCMG_MAX_LEVELS];   // FP64 blocks [S][C][np][np]
+  const int* nbr[KCMG_MAX_LEVELS];
+  const double* P;                       // [2^dim][np][np]
+  const double* Ainv;                    // dense inverse of the coarsest operator
+  int Nc;
+  double omega;
+  int sweeps;
+  double lvl_rtol[KCMG_MAX_LEVELS];
+  int lvl_maxit[KCMG_MAX_LEVELS];
+  int lmax;
+  int precision;                         // kcmg_precision
+  int tc_tf32_only;                      // single-product TF32 sweeps
+  cudaStream_t s;
+};
+
+struct MrhsEngine;
+// Solve A X = B for R = nrhs columns (X holds X0 on entry).  Returns the status; on a
+// failure *err receives a message.
+kcmg_status mrhs_solve(MrhsEngine** eng, const MrhsView& v, const double* b, double* x, int nrhs,
+                       double rtol, double atol, int maxiter, kcmg_info* info, std::string* err);
+// Build (or rebuild for another nrhs / precision) the engine without solving.
+kcmg_status mrhs_ensure(MrhsEngine** eng, const MrhsView& v, int nrhs, std::string* err);
+// Batched component calls on an ensured engine (host or device pointers, [N_level][R]).
+kcmg_status mrhs_apply(MrhsEngine* eng, int level, const double* x, double* y);
+kcmg_status mrhs_smooth(MrhsEngine* eng, int level, const double* r, double* z);
+// Launch shapes the autotuner chose (out[0..nout)), see kcmg_mrhs_tuning.
+int mrhs_tuning(const MrhsEngine* eng, double* out, int nout);
+void mrhs_destroy(MrhsEngine* eng);
 
 int block_rows_for(int np);  // threads per block of the operator kernels (whole cells)
 bool np_supported(int np, int dim);

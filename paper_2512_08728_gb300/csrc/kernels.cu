@@ -195,6 +195,77 @@ __device__ __forceinline__ void finish_reduction(double (&v)[NC], double* partia
 // y = A x (or y = b - A x), one thread per DOF row, optional ||y||^2 with an epilogue.
 // conditional: run only if the level requested a restart; otherwise thread 0 of block 0
 // re-evaluates the loop condition and every block returns.
+// Error-free transformations for the compensated residual (Knuth's two-sum; the product
+// error from a fused multiply-add).
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
+  s = a + b;
+  const double bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// r = b - A x with the products and sums of each row carried in double-double and rounded
+// once: the correctly rounded residual of the FP64 iterate, so that convergence tests near
+// the attainable accuracy are not decided by summation noise.  ||r||^2 with an epilogue.
+template <int NP, int S>
+__device__ __forceinline__ double residual_dd_row(const double* __restrict__ A, const int* __restrict__ nbr,
+                                                  int G, int row, const double* __restrict__ x,
+                                                  double bv) {
+  constexpr int JP = (NP + 1) / 2;
+  constexpr int NF = S - 1;
+  const int g = row >> 5, lane = row & 31, K = row / NP;
+  double hi = 0.0, lo = 0.0;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int J = (s == 0) ? K : __ldg(nbr + (size_t)K * NF + s - 1);
+    if (J < 0) continue;
+    const double2* Ap = reinterpret_cast<const double2*>(A) + ((size_t)(s * G + g) * JP) * 32 + lane;
+    const double* xp = x + (size_t)J * NP;
+#pragma unroll
+    for (int jp = 0; jp < JP; ++jp) {
+      const double2 a = __ldg(Ap + jp * 32);
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (2 * jp + q >= NP) continue;
+        const double av = q ? a.y : a.x, xv = __ldg(xp + 2 * jp + q);
+        const double p = av * xv, pe = fma(av, xv, -p);
+        double sh, se;
+        two_sum(hi, p, sh, se);
+        hi = sh;
+        lo += se + pe;
+      }
+    }
+  }
+  double t, te;
+  two_sum(bv, -hi, t, te);
+  return t + (te - lo);
+}
+
+template <int NP, int S>
+__global__ void __launch_bounds__(320)
+k_residual_dd(const double* __restrict__ A, const int* __restrict__ nbr, int N, int G,
+              const double* __restrict__ x, double* __restrict__ r, const double* __restrict__ b,
+              double* partial, EpiArgs e, int conditional) {
+  if (conditional) {   // end of a loop body: count it, then restart or set the condition
+    if (!e.st->restart_req) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        e.st->guard++;
+        set_cond(e, more_cycles(e.st));
+      }
+      return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&e.st->guard, 1);
+  }
+  __shared__ double sh[32];
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  double out = 0.0;
+  if (row < N) {
+    out = residual_dd_row<NP, S>(A, nbr, G, row, x, b[row]);
+    r[row] = out;
+  }
+  double v[1] = {out * out};
+  finish_reduction<1>(v, partial, e, sh);
+}
+
 template <typename T, int NP, int S, bool RESID, bool NORM>
 __global__ void __launch_bounds__(320)
 k_spmv(const T* __restrict__ A, const int* __restrict__ nbr, int N, int G,
@@ -406,11 +477,15 @@ k_gram_dots(const T* __restrict__ W, int N, const T* __restrict__ w, double* par
     }
   }
   if (last_block(&st->ticket)) {
+    // one warp per column: lanes read independent partials, then a fixed shuffle tree
     extern __shared__ double sums[];  // [ncol]
-    for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+    const int wid = threadIdx.x >> 5, ln = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int c = wid; c < ncol; c += nw) {
       double s = 0.0;
-      for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(partial + (size_t)b * ncol + c);
-      sums[c] = s;
+      for (int b = ln; b < (int)gridDim.x; b += 32) s += __ldcg(partial + (size_t)b * ncol + c);
+#pragma unroll
+      for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (ln == 0) sums[c] = s;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -887,6 +962,15 @@ void launch_spmv(int np, int dim, const T* A, const int* nbr, int N, int G, int 
     else if (resid) k_spmv<T, NP, S, true, false><<<grid, block_rows, 0, s>>>(A, nbr, N, G, x, y, b, partial, e, conditional);
     else if (norm) k_spmv<T, NP, S, false, true><<<grid, block_rows, 0, s>>>(A, nbr, N, G, x, y, b, partial, e, conditional);
     else k_spmv<T, NP, S, false, false><<<grid, block_rows, 0, s>>>(A, nbr, N, G, x, y, b, partial, e, conditional);
+  });
+}
+
+void launch_residual_dd(int np, int dim, const double* A, const int* nbr, int N, int G, int rows_pad,
+                        int block_rows, const double* x, double* r, const double* b, double* partial,
+                        const EpiArgs& e, int conditional, cudaStream_t s) {
+  const int grid = rows_pad / block_rows;
+  KCMG_ND_SWITCH(np, dim, {
+    k_residual_dd<NP, S><<<grid, block_rows, 0, s>>>(A, nbr, N, G, x, r, b, partial, e, conditional);
   });
 }
 

@@ -26,7 +26,8 @@ class kcmg_params(C.Structure):
                 ("blocks", C.c_void_p), ("prolong", C.c_void_p), ("omega", C.c_double),
                 ("sweeps", C.c_int), ("lvl_rtol", C.c_double * KCMG_MAX_LEVELS),
                 ("lvl_maxit", C.c_int * KCMG_MAX_LEVELS), ("lmax", C.c_int),
-                ("precision", C.c_int), ("use_graph", C.c_int), ("coarse_persistent", C.c_int)]
+                ("precision", C.c_int), ("use_graph", C.c_int), ("coarse_persistent", C.c_int),
+                ("tc_tf32_only", C.c_int)]
 
 
 class kcmg_info(C.Structure):
@@ -71,6 +72,9 @@ def load_library():
         "kcmg_level_cells": (ip, [vp, ip]),
         "kcmg_kernel_report": (ip, [vp, ip, vp, ip]),
         "kcmg_residual_noalloc": (ip, [vp, vp, vp, vp, C.POINTER(C.c_double)]),
+        "kcmg_mrhs_tuning": (ip, [vp, vp, ip]),
+        "kcmg_apply_multi": (ip, [vp, ip, ip, vp, vp]),
+        "kcmg_smooth_multi": (ip, [vp, ip, ip, vp, vp]),
         "kcmg_last_error": (C.c_char_p, [vp]),
         "kcmg_status_string": (C.c_char_p, [ip]),
         "kcmg_destroy": (None, [vp]),
@@ -88,7 +92,8 @@ def exported_symbols():
     return ["kcmg_default_params", "kcmg_setup", "kcmg_solve", "kcmg_solve_adjoint",
             "kcmg_grad_lognu", "kcmg_apply", "kcmg_smooth", "kcmg_restrict", "kcmg_prolong",
             "kcmg_coarse_solve", "kcmg_get_blocks", "kcmg_rm_sequence", "kcmg_level_cells",
-            "kcmg_kernel_report", "kcmg_residual_noalloc",
+            "kcmg_kernel_report", "kcmg_residual_noalloc", "kcmg_mrhs_tuning",
+            "kcmg_apply_multi", "kcmg_smooth_multi",
             "kcmg_last_error", "kcmg_status_string", "kcmg_destroy"]
 
 
@@ -181,19 +186,52 @@ def _info_dict(st, info, hist, htype):
 
 
 def kcmg_solve(ctx, b, x, rtol=1e-10, atol=0.0, maxiter=500, hist_cap=4096, adjoint=False):
-    """Solve in place: x holds x0 on entry and the solution on return."""
+    """Solve in place: x holds x0 on entry and the solution on return.  b, x: [N] or
+    [N, nrhs] (nrhs <= 32, right-hand sides fastest)."""
     lib = load_library()
+    if tuple(b.shape) != tuple(x.shape) or len(b.shape) not in (1, 2):
+        raise ValueError("b and x must have the same shape [N] or [N, nrhs]")
+    nrhs = 1 if len(b.shape) == 1 else int(b.shape[1])
     pb, kb = _ptr(b)
     px, kx = _ptr(x, write=True)
     info, hist, htype = _info(hist_cap)
     f = lib.kcmg_solve_adjoint if adjoint else lib.kcmg_solve
-    st = f(ctx, pb, px, 1, float(rtol), float(atol), int(maxiter), C.byref(info))
+    st = f(ctx, pb, px, nrhs, float(rtol), float(atol), int(maxiter), C.byref(info))
     _check(ctx, st)
     return _info_dict(st, info, hist, htype)
 
 
 def kcmg_solve_adjoint(ctx, g, lam, rtol=1e-10, atol=0.0, maxiter=500, hist_cap=4096):
     return kcmg_solve(ctx, g, lam, rtol, atol, maxiter, hist_cap, adjoint=True)
+
+
+def _multi(name, ctx, level, a):
+    if len(a.shape) != 2:
+        raise ValueError("expected an [N, nrhs] array")
+    out = _empty_like(a, tuple(a.shape))
+    pa, ka = _ptr(_f64(a))
+    po, ko = _ptr(out, write=True)
+    _check(ctx, getattr(load_library(), name)(ctx, level, int(a.shape[1]), pa, po))
+    return out
+
+
+def kcmg_apply_multi(ctx, level, x):
+    """Y = A_level X for X [N_level, nrhs] (FP64 batched operator kernel)."""
+    return _multi("kcmg_apply_multi", ctx, level, x)
+
+
+def kcmg_smooth_multi(ctx, level, r):
+    """Z = BJ_level(R) for R [N_level, nrhs] (batched sweeps in the context's precision)."""
+    return _multi("kcmg_smooth_multi", ctx, level, r)
+
+
+def kcmg_mrhs_tuning(ctx):
+    """Launch shapes the multi-right-hand-side autotuner chose (see kcmg.h)."""
+    out = np.zeros(8)
+    _check(ctx, load_library().kcmg_mrhs_tuning(ctx, out.ctypes.data, out.size))
+    keys = ["spmm_warps", "spmm_ms", "sweep_warps", "sweep_grid", "sweep_ms", "lcap0", "nrhs",
+            "x3"]
+    return dict(zip(keys, out.tolist()))
 
 
 def kcmg_level_cells(ctx, level):
@@ -287,7 +325,8 @@ class KCycleSolver:
     """Owns one kcmg context built from a workloads.Problem-like object."""
 
     def __init__(self, problem, precision="fp64", use_graph=True, omega=0.7, sweeps=5,
-                 lmax=0, lvl_rtol=None, lvl_maxit=None, coarse_persistent=True, stream=None):
+                 lmax=0, lvl_rtol=None, lvl_maxit=None, coarse_persistent=True, stream=None,
+                 tc_tf32_only=0):
         pr = problem
         self.dim, self.np_, self.nlevels = pr.d, pr.np_, pr.nlevels
         self.ndof = pr.ndof
@@ -296,6 +335,7 @@ class KCycleSolver:
         p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         p.use_graph = int(use_graph)
         p.coarse_persistent = int(coarse_persistent)
+        p.tc_tf32_only = int(tc_tf32_only)
         if lvl_rtol is not None:
             for i, v in enumerate(lvl_rtol):
                 p.lvl_rtol[i] = v
@@ -316,7 +356,7 @@ class KCycleSolver:
     def solve(self, b, x0=None, rtol=1e-10, atol=0.0, maxiter=500, adjoint=False):
         b = _f64(b)
         if x0 is None:
-            x = _empty_like(b, b.shape[0])
+            x = _empty_like(b, tuple(b.shape))
             x[:] = 0
         else:
             x = _f64(x0).clone() if _is_torch(x0) else _f64(x0).copy()
@@ -343,6 +383,15 @@ class KCycleSolver:
 
     def rm_sequence(self, level, b, x0, zs):
         return kcmg_rm_sequence(self.ctx, level, b, x0, zs, self.np_)
+
+    def apply_multi(self, level, x):
+        return kcmg_apply_multi(self.ctx, level, x)
+
+    def smooth_multi(self, level, r):
+        return kcmg_smooth_multi(self.ctx, level, r)
+
+    def mrhs_tuning(self):
+        return kcmg_mrhs_tuning(self.ctx)
 
     def kernel_report(self, reps=0):
         return kcmg_kernel_report(self.ctx, reps)

@@ -160,6 +160,80 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+MRHS_WORKLOAD = "sipg3d_p2_32cube_rhs32"
+MRHS_LMAX = 100
+MRHS_PRECISION = "mixed_bf16"
+
+
+def run_mrhs(pkg, rank, dev, stream, hbm_peak, args):
+    """The batched form: 32 right-hand sides solved together (one K-cycle per column,
+    shared operator applications, tensor-core sweeps).  value = DOFs x columns / s."""
+    import torch
+
+    from workloads import workload
+    pm = workload(MRHS_WORKLOAD).make(rank)
+    B = torch.from_numpy(pm.b).to(dev)
+    X = torch.zeros_like(B)
+    sm = pkg.KCycleSolver(pm, precision=MRHS_PRECISION, lmax=MRHS_LMAX, stream=stream.cuda_stream)
+    pkg.kcmg_solve(sm.ctx, B, X, RTOL, 0.0, 1)   # build the batched engine and autotune
+    tune = sm.mrhs_tuning()
+    X.zero_()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    inf = pkg.kcmg_solve(sm.ctx, B, X, RTOL, 0.0, args.maxiter)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    mms = e0.elapsed_time(e1)
+    # the same operator solved one column at a time (columns 0 and 1, FP64 and the same
+    # mixed form) for comparison
+    single = {}
+    for prec in ("fp64", MRHS_PRECISION):
+        s1 = pkg.KCycleSolver(pm, precision=prec, use_graph=True, lmax=200, stream=stream.cuda_stream)
+        ts = []
+        for j in (0, 1):
+            bj = B[:, j].contiguous()
+            xj = torch.zeros_like(bj)
+            pkg.kcmg_solve(s1.ctx, bj, xj, RTOL, 0.0, 2)
+            xj.zero_()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            ij = pkg.kcmg_solve(s1.ctx, bj, xj, RTOL, 0.0, args.maxiter)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append((e0.elapsed_time(e1), ij["iters"]))
+        s1.close()
+        single[prec] = {"value": pm.ndof * len(ts) / (sum(t for t, _ in ts) * 1e-3), "unit": UNIT,
+                        "cycles": [c for _, c in ts]}
+    sm.close()
+    R = int(pm.b.shape[1])
+    C = pm.ndof // pm.np_
+    np2, S = pm.np_ * pm.np_, 2 * pm.d + 1
+    inv_b = 2 if MRHS_PRECISION == "mixed_bf16" else 4
+    # algorithmic bytes of one tensor-core sweep (sweeps 2..5): FP32 off-diagonal blocks,
+    # stored inverses, r (FP32) and the old and new iterates (FP32), each once
+    sweep_bytes = C * ((S - 1) * np2 * 4 + np2 * inv_b) + 3 * pm.ndof * R * 4
+    sweep_gbs = sweep_bytes / (tune["sweep_ms"] * 1e-3) / 1e9 if tune["sweep_ms"] > 0 else 0.0
+    # FP64 block SpMM: one FMA per block element and column
+    spmm_tflops = 2.0 * S * np2 * C * R / (tune["spmm_ms"] * 1e-3) / 1e12 if tune["spmm_ms"] > 0 else 0.0
+    return {
+        "value": pm.ndof * R / (mms * 1e-3), "unit": UNIT, "workload": MRHS_WORKLOAD, "nrhs": R,
+        "ms_per_step": mms, "status": inf["status"], "rel_res": inf["rel_res"],
+        "cycles": inf["iters"], "level_iters": inf["level_iters"][:pm.nlevels],
+        "lmax": MRHS_LMAX, "kernel_launches": inf["kernel_launches"],
+        "single_column_solves": single,
+        "dtype": "tensor-core TF32x3 smoother sweeps (FP32 accumulation), BF16 block inverses; "
+                 "f64 residual minimisation, transfers, coarsest solve",
+        "autotuner": tune,
+        "sweep_tc": {"bound": "hbm", "achieved": sweep_gbs, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": sweep_gbs / hbm_peak, "bytes_per_launch": sweep_bytes,
+                     "ms_per_launch": tune["sweep_ms"]},
+        "spmm_fp64": {"bound": "alu", "achieved": spmm_tflops, "peak": FP64_TFLOPS,
+                      "unit": "TFLOP/s", "frac": spmm_tflops / FP64_TFLOPS,
+                      "ms_per_launch": tune["spmm_ms"]},
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -169,6 +243,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mrhs", action="store_true",
+                    help="also solve a 32-right-hand-side batch (32^3 p=2, 32 columns of U[-1,1]) "
+                         "in the batched mixed form, with single-column solves of the same "
+                         "operator beside it, and report it under forms")
     ap.add_argument("--maxiter", type=int, default=MAXITER,
                     help="cap on level-0 cycles (profiling runs only; the benchmark solves to 1e-10)")
     ap.add_argument("--workload", default=WORKLOAD, help="workload name (profiling runs only)")
@@ -251,7 +329,8 @@ def main():
          "achieved": coarse_gbs, "peak": hbm_peak, "unit": "GB/s",
          "frac": coarse_gbs / hbm_peak, "ms_per_launch": coarse_ms,
          "bytes_per_launch": coarse_bytes, "share_of_step": share,
-         "ms_per_launch_by_level": [v / cl for v in rep["coarse_level_ms"][:pr.nlevels]]},
+         "ms_per_launch_by_level": [v / cl for v in rep["coarse_level_ms"][:pr.nlevels]],
+         "ms_per_launch_by_phase": {k: v / cl for k, v in rep["coarse_phase_ms"].items()}},
         {"name": "k_spmv level 0 FP64 (Alg. 1 operator)", "bound": "alu",
          "achieved": rep["spmv_bytes"] / (rep["spmv_ms"] * 1e-3) / 1e9,
          "peak": fp64_gbs, "unit": "GB/s",
@@ -310,6 +389,9 @@ def main():
                                     / (rp["coarse_ms"] / max(1, rp["coarse_launches"]) * 1e-3) / 1e9
                                     if rp["coarse_ms"] > 0 else None}
             sm.close()
+
+    if args.mrhs:
+        forms["mrhs32"] = run_mrhs(pkg, rank, dev, stream, hbm_peak, args)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -100,7 +100,8 @@ void kcmg_default_params(kcmg_params *p, int dim, int np, const int n[3], int nl
 
 /* Convergence report.  hist/hist_type are caller-owned arrays of length hist_cap (may be
    NULL): ||r|| after every level-0 RM call with type 0 initial, 1 pre-smoother, 2 coarse
-   correction, 3 post-smoother, 4 restart (true residual replaces the recursive one). */
+   correction, 3 post-smoother, 4 restart (true residual replaces the recursive one);
+   batched solves record instead the active columns at each level-0 loop test (type 5). */
 typedef struct {
     int iters;                          /* level-0 cycles */
     int level_iters[KCMG_MAX_LEVELS];   /* cycles per level, summed over visits */
@@ -137,7 +138,8 @@ kcmg_status kcmg_setup(kcmg_ctx **out, const kcmg_params *p, void *cuda_stream);
    (TF32 products, FP32 accumulation), with launch shapes chosen by an autotuner at the
    first batched solve (see kcmg_mrhs_tuning).  info: iters and level_iters count the
    shared loop; rel_res is the largest relative residual over the columns and res0 the
-   largest initial residual; no history is recorded. */
+   largest initial residual; the history records the number of active columns at every
+   level-0 loop test (hist_type 5). */
 kcmg_status kcmg_solve(kcmg_ctx *ctx, const double *b, double *x, int nrhs, double rtol,
                        double atol, int maxiter, kcmg_info *info);
 
@@ -184,7 +186,11 @@ kcmg_status kcmg_rm_sequence(kcmg_ctx *ctx, int level, const double *b, const do
    (out[3] ms per launch, out[4] algorithmic bytes) and of one full block-Jacobi sweep in
    the smoother's precision (out[5] ms, out[6] bytes).  out[7 + l] (if nout allows): device
    milliseconds the coarse-cycle kernel spent on level l (the coarsest: its direct solves).
-   nout >= 7. */
+   out[19 + k] (if nout allows): milliseconds it spent in phases of kind k, each with its
+   closing grid barrier: 0 block-Jacobi sweep, 1 w = A z with the first Gram pass and its
+   reduction, 2 second Gram pass, 3 new basis column with its norms, 4 normalisation and
+   x, r update, 5 restriction or prolongation, 6 coarsest solve, 7 restart residual,
+   8 level entry and return.  nout >= 7. */
 kcmg_status kcmg_kernel_report(kcmg_ctx *ctx, int reps, double *out, int nout);
 
 /* r = b - A x with the finest-level FP64 operator, and *rnorm = ||r|| (a host double),

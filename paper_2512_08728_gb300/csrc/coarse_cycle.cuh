@@ -11,6 +11,7 @@
 // block leaves the kernel, so a fault becomes a status, not a hang.
 #pragma once
 #include "kcmg_internal.h"
+#include "reduce.cuh"
 
 #include <cuda/atomic>
 
@@ -60,31 +61,6 @@ __device__ __forceinline__ double bsum(double v, double* sh) {
     for (int o = 16; o; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
   }
   return r;  // valid in thread 0
-}
-
-// NC block sums at once (one shared-memory exchange): results valid in thread 0.
-// sh: >= 32 * NC doubles.
-template <int NC>
-__device__ __forceinline__ void bsum_n(double (&v)[NC], double* sh) {
-#pragma unroll
-  for (int c = 0; c < NC; ++c)
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
-  const int w = threadIdx.x >> 5, ln = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
-  __syncthreads();
-  if (ln == 0)
-#pragma unroll
-    for (int c = 0; c < NC; ++c) sh[c * 32 + w] = v[c];
-  __syncthreads();
-  if (w == 0) {
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      double r = (ln < nw) ? sh[c * 32 + ln] : 0.0;
-#pragma unroll
-      for (int o = 16; o; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
-      v[c] = r;
-    }
-  }
 }
 
 template <typename T> __device__ __forceinline__ T ldv(const T* p) { return __ldcg(p); }
@@ -261,7 +237,7 @@ struct CoarseCycle {
       const T sum = (acc[0] + acc[1]) + (acc[2] + acc[3]);
       const T out = b ? (ldv(b + row) - sum) : sum;
       y[row] = out;
-      nrm += (double)out * (double)out;
+      nrm = fma((double)out, (double)out, nrm);
     }
     return nrm;
   }
@@ -333,6 +309,7 @@ struct CoarseCycle {
       if (k == a.sweeps - 1) sweep<T>(C, r, zo, out, k == 0);
       else sweep<TS>(C, r, zo, sb[k & 1], k == 0);
       ok = bar();
+      ph(PH_SWEEP);
     }
     return out;
   }
@@ -357,6 +334,7 @@ struct CoarseCycle {
     dots(W, N, w, l, part);
     count((double)(l + 1) * N * 8);
     if (!reduce_cols(part, nc)) return false;
+    ph(PH_RM_GRAM1);
     double hh = 0.0;
     for (int i = 0; i < l; ++i) hh += red_s[i] * red_s[i];
     const double naz2 = red_s[l];
@@ -385,6 +363,7 @@ struct CoarseCycle {
       }
       __syncthreads();
       wsrc = wre;
+      ph(PH_RM_REORTH);
     }
     // w_hat = wsrc - W cw, z_hat = z - Z cz into column l; ||w_hat||^2, w_hat . r
     T* Wl = W + (size_t)l * N;
@@ -407,14 +386,15 @@ struct CoarseCycle {
       zv += zv1;
       Wl[j] = av;
       Zl[j] = zv;
-      nw2 += (double)(av * av);
-      wr += (double)(av * ldv(r + j));
+      nw2 = fma((double)av, (double)av, nw2);
+      wr = fma((double)av, (double)ldv(r + j), wr);
     }
     count((double)(2 * l + 5) * N * 8);   // W, Z columns; w, z, r in; new columns out
     {
       double v[2] = {nw2, wr};
       if (!reduce_few<2>(v)) return false;
     }
+    ph(PH_RM_UPDATE);
     const double nw = sqrt(red_s[0]);
     if (!isfinite(nw) || !(nw > a.brk * sqrt(naz2))) discard = true;
     const double gam = discard ? 0.0 : 1.0 / nw;
@@ -434,7 +414,7 @@ struct CoarseCycle {
         rv = fma(-al, wv, rv);
         rr[j] = rv;
       }
-      r2 += (double)(rv * rv);
+      r2 = fma((double)rv, (double)rv, r2);
     }
     count(discard ? 0.0 : (double)N * 8 * 8);
     // ||r - alpha w||^2 = ||r||^2 - alpha^2 for unit w with alpha = w . r; reduce the
@@ -451,6 +431,7 @@ struct CoarseCycle {
       sc.rnorm = sqrt(red_s[0]);
     }
     if (!discard) sc.l++;
+    ph(PH_RM_FINISH);
     return true;
   }
 
@@ -462,14 +443,12 @@ struct CoarseCycle {
 #pragma unroll
       for (int c = 0; c < 8; ++c) acc[c] = 0.0;
       for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
-        const T wv = ldv(w + j);
+        const double wv = (double)ldv(w + j);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
           const int col = c0 + c;
-          T p = T(0);
-          if (col < l) p = ldv(W + (size_t)col * N + j) * wv;
-          else if (col == l) p = wv * wv;
-          acc[c] += (double)p;
+          if (col < l) acc[c] = fma((double)ldv(W + (size_t)col * N + j), wv, acc[c]);
+          else if (col == l) acc[c] = fma(wv, wv, acc[c]);
         }
       }
       bsum_n<8>(acc, sh);
@@ -504,7 +483,7 @@ struct CoarseCycle {
         vec(C.r)[row] = s;
         vec(C.x)[row] = T(0);
       }
-      nrm += (double)s * (double)s;
+      nrm = fma((double)s, (double)s, nrm);
     }
     return nrm;
   }
@@ -557,6 +536,18 @@ struct CoarseCycle {
     sc.eps = L(lev).rtol * sc.rnorm0;
   }
 
+  // time attribution per phase kind (thread 0 of block 0; the interval since the previous
+  // phase boundary, closing barrier included)
+  unsigned long long t_ph = 0;
+  __device__ void ph(int kind) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      unsigned long long t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if (t_ph) atomicAdd(a.stat_phase_ns + kind, t - t_ph);
+      t_ph = t;
+    }
+  }
+
   // time attribution per level (thread 0 of block 0)
   unsigned long long t_mark = 0;
   __device__ void mark(int lev) {
@@ -576,6 +567,7 @@ struct CoarseCycle {
     for (int i = 0; i < KCMG_MAX_LEVELS; ++i) { phase[i] = TEST; restarts[i] = 0; guard[i] = 0; }
     int lev = lev0;
     mark(lev);
+    ph(PH_CONTROL);
     sc[lev].rnorm0 = red_s[0];
     sc[lev].rnorm0 = sqrt(sc[lev].rnorm0);
     start(lev, sc[lev]);
@@ -593,6 +585,7 @@ struct CoarseCycle {
           if (lev == lev0) break;
           --lev;                                                   // return to the caller
           if (!(ok = bar())) break;
+          ph(PH_CONTROL);
           continue;
         }
         ++guard[lev];
@@ -604,13 +597,16 @@ struct CoarseCycle {
         phase[lev] = AFTER_COARSE;
         if (direct) {
           if (!(ok = bar())) break;
+          ph(PH_TRANSFER);
           mark(lev);
           coarse_solve(lev + 1);                                   // z_c = A_c \ r_c
           if (!(ok = bar())) break;
+          ph(PH_COARSEST);
           mark(lev + 1);
         } else {
           double v[1] = {nb};
           if (!(ok = reduce_few<1>(v))) break;
+          ph(PH_TRANSFER);
           mark(lev);
           ++lev;                                                   // z_c = MG(A_c, r_c, 0)
           sc[lev].rnorm0 = sqrt(red_s[0]);
@@ -622,6 +618,7 @@ struct CoarseCycle {
       // AFTER_COARSE: prolongate, minimise, post-smooth, minimise
       prolong(lev);                                                // z = P z_c
       if (!(ok = bar())) break;
+      ph(PH_TRANSFER);
       if (!(ok = rm(lev, vec(C.z), s))) break;
       T* z = smooth(lev, vec(C.r));                                // post-smoother
       if (!ok || !(ok = rm(lev, z, s))) break;
@@ -631,6 +628,7 @@ struct CoarseCycle {
         if (!(ok = bar())) break;
         double v[1] = {spmv(lev, vec(C.x), vec(C.r), vec(C.b))};
         if (!(ok = reduce_few<1>(v))) break;
+        ph(PH_RESTART);
         s.rnorm = sqrt(red_s[0]);
         s.l = 0;
         ++restarts[lev];

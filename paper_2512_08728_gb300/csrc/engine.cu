@@ -74,6 +74,7 @@ struct kcmg_ctx {
   unsigned long long* stat_launches = nullptr;
   double* stat_bytes = nullptr;
   unsigned long long* stat_level_ns = nullptr;
+  unsigned long long* stat_phase_ns = nullptr;
   kcmg_ctx* adj = nullptr;       // transposed hierarchy (may be this)
   MrhsEngine* mrhs = nullptr;    // batched multi-right-hand-side solver (built on demand)
   bool adj_built = false;
@@ -885,6 +886,9 @@ kcmg_ctx* build_ctx(const kcmg_params* p, cudaStream_t user, const double* block
       ctx->stat_level_ns = dalloc<unsigned long long>(ctx, KCMG_MAX_LEVELS);
       CK(cudaMemsetAsync(ctx->stat_level_ns, 0, 8 * KCMG_MAX_LEVELS, ctx->s));
       a.stat_level_ns = ctx->stat_level_ns;
+      ctx->stat_phase_ns = dalloc<unsigned long long>(ctx, kCoarsePhases);
+      CK(cudaMemsetAsync(ctx->stat_phase_ns, 0, 8 * kCoarsePhases, ctx->s));
+      a.stat_phase_ns = ctx->stat_phase_ns;
       CK(cudaMemsetAsync(ctx->stat_ns, 0, 8, ctx->s));
       CK(cudaMemsetAsync(ctx->stat_launches, 0, 8, ctx->s));
       CK(cudaMemsetAsync(ctx->stat_bytes, 0, 8, ctx->s));
@@ -1193,8 +1197,13 @@ kcmg_status kcmg_kernel_report(kcmg_ctx* ctx, int reps, double* out, int nout) {
       unsigned long long lns[KCMG_MAX_LEVELS] = {0};
       CK(cudaMemcpyAsync(lns, ctx->stat_level_ns, sizeof lns, cudaMemcpyDeviceToHost, ctx->s));
       CK(cudaMemsetAsync(ctx->stat_level_ns, 0, sizeof lns, ctx->s));
+      unsigned long long pns[kCoarsePhases] = {0};
+      CK(cudaMemcpyAsync(pns, ctx->stat_phase_ns, sizeof pns, cudaMemcpyDeviceToHost, ctx->s));
+      CK(cudaMemsetAsync(ctx->stat_phase_ns, 0, sizeof pns, ctx->s));
       CK(cudaStreamSynchronize(ctx->s));
       for (int l = 0; l < KCMG_MAX_LEVELS && 7 + l < nout; ++l) out[7 + l] = lns[l] * 1e-6;
+      for (int k = 0; k < kCoarsePhases && 7 + KCMG_MAX_LEVELS + k < nout; ++k)
+        out[7 + KCMG_MAX_LEVELS + k] = pns[k] * 1e-6;
       CK(cudaMemsetAsync(ctx->stat_ns, 0, 8, ctx->s));
       CK(cudaMemsetAsync(ctx->stat_launches, 0, 8, ctx->s));
       CK(cudaMemsetAsync(ctx->stat_bytes, 0, 8, ctx->s));

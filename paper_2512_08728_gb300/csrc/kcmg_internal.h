@@ -145,6 +145,19 @@ void launch_grad_lognu(int np, int dim, const int* n, const double* nu, const do
 
 // ---------------------------------------------------------------- coarse cycle kernel
 constexpr int kCoarseMaxCols = 128;   // basis capacity + 1 on the coarse levels
+// phase kinds timed inside the persistent coarse cycle (each includes its closing barrier)
+enum CoarsePhase : int {
+  PH_SWEEP = 0,      // one block-Jacobi sweep
+  PH_RM_GRAM1,       // w = A z, W^T w, ||w||^2 and their grid reduction
+  PH_RM_REORTH,      // second Gram-Schmidt pass
+  PH_RM_UPDATE,      // new basis column, ||w_hat||^2, w_hat . r
+  PH_RM_FINISH,      // normalisation, x and r update
+  PH_TRANSFER,       // restriction (with ||b_c||) or prolongation
+  PH_COARSEST,       // dense solve on the coarsest level
+  PH_RESTART,        // r = b - A x on a level restart
+  PH_CONTROL,        // level entry and return
+  kCoarsePhases
+};
 
 struct CoarseLevel {
   const void* A;        // row-interleaved FP64 operator (residual minimisation)
@@ -180,6 +193,7 @@ struct CoarseArgs {
   unsigned long long* stat_launches;
   double* stat_bytes;
   unsigned long long* stat_level_ns;   // [KCMG_MAX_LEVELS] time spent on each level
+  unsigned long long* stat_phase_ns;   // [kCoarsePhases] time spent in each kind of phase
   int smoother_bytes;          // bytes per element of the smoother operator
   int inverse_bytes;           // bytes per element of the stored block inverses
 };

@@ -4,6 +4,7 @@
 // residual-minimisation kernels of Alg. 1, the device-side loop control of Alg. 2 and
 // the setup kernels (Galerkin product, block inverses, dense coarsest inverse).
 #include "kcmg_internal.h"
+#include "reduce.cuh"
 
 #include <cmath>
 
@@ -176,11 +177,10 @@ __device__ void epilogue(const EpiArgs& e, const double* sums) {
 template <int NC>
 __device__ __forceinline__ void finish_reduction(double (&v)[NC], double* partial, const EpiArgs& e,
                                                  double* sh) {
+  bsum_n<NC>(v, sh);
+  if (threadIdx.x == 0)
 #pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    double s = block_sum(v[c], sh);
-    if (threadIdx.x == 0) partial[(size_t)blockIdx.x * NC + c] = s;
-  }
+    for (int c = 0; c < NC; ++c) partial[(size_t)blockIdx.x * NC + c] = v[c];
   if (last_block(&e.st->ticket)) {
     __shared__ double sums[NC];
     reduce_few(partial, gridDim.x, NC, sums, sh);
@@ -255,7 +255,7 @@ k_residual_dd(const double* __restrict__ A, const int* __restrict__ nbr, int N, 
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&e.st->guard, 1);
   }
-  __shared__ double sh[32];
+  __shared__ double sh[32 * 8];   // bsum_n<NC> needs 32 * NC
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   double out = 0.0;
   if (row < N) {
@@ -285,7 +285,7 @@ k_spmv(const T* __restrict__ A, const int* __restrict__ nbr, int N, int G,
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&e.st->guard, 1);
   }
-  __shared__ double sh[32];
+  __shared__ double sh[32 * 8];   // bsum_n<NC> needs 32 * NC
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   const int g = row >> 5, lane = row & 31;
   T acc = T(0);
@@ -378,7 +378,7 @@ k_restrict(Dims nf, Dims nc, const T* __restrict__ P, const TIN* __restrict__ rf
            T* rout, T* xout, int Nc, double* partial, EpiArgs e) {
   constexpr int NCH = 1 << DIM;
   __shared__ T Ps[NCH * NP * NP];
-  __shared__ double sh[32];
+  __shared__ double sh[32 * 8];   // bsum_n<NC> needs 32 * NC
   for (int i = threadIdx.x; i < NCH * NP * NP; i += blockDim.x) Ps[i] = P[i];
   __syncthreads();
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
@@ -447,7 +447,7 @@ k_gram_dots(const T* __restrict__ W, int N, const T* __restrict__ w, double* par
             EpiArgs e, int conditional) {
   LevelState* st = e.st;
   if (conditional && !(st->flags & F_REORTH)) return;
-  __shared__ double sh[32];
+  __shared__ double sh[32 * 8];   // bsum_n<NC> needs 32 * NC
   const int l = st->l;
   const int ncol = l + 1;
   const int chunk = (N + gridDim.x - 1) / gridDim.x;
@@ -457,24 +457,19 @@ k_gram_dots(const T* __restrict__ W, int N, const T* __restrict__ w, double* par
 #pragma unroll
     for (int c = 0; c < 8; ++c) acc[c] = 0.0;
     for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-      const T wv = w[j];
-      T a[8];
-#pragma unroll
-      for (int c = 0; c < 8; ++c) a[c] = T(0);
+      const double wv = (double)w[j];
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         const int col = c0 + c;
-        if (col < l) a[c] = __ldg(W + (size_t)col * N + j) * wv;
-        else if (col == l) a[c] = wv * wv;
+        if (col < l) acc[c] = fma((double)__ldg(W + (size_t)col * N + j), wv, acc[c]);
+        else if (col == l) acc[c] = fma(wv, wv, acc[c]);
       }
-#pragma unroll
-      for (int c = 0; c < 8; ++c) acc[c] += (double)a[c];
     }
+    bsum_n<8>(acc, sh);
+    if (threadIdx.x == 0)
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const double s = block_sum(acc[c], sh);
-      if (threadIdx.x == 0 && c0 + c < ncol) partial[(size_t)blockIdx.x * ncol + c0 + c] = s;
-    }
+      for (int c = 0; c < 8; ++c)
+        if (c0 + c < ncol) partial[(size_t)blockIdx.x * ncol + c0 + c] = acc[c];
   }
   if (last_block(&st->ticket)) {
     // one warp per column: lanes read independent partials, then a fixed shuffle tree
@@ -522,7 +517,7 @@ k_gram_update(T* W, T* Z, int N, const T* __restrict__ w, const T* __restrict__ 
               const T* __restrict__ z, const T* __restrict__ r, double* partial, EpiArgs e) {
   LevelState* st = e.st;
   extern __shared__ double cs[];  // [2][l]
-  __shared__ double sh[32];
+  __shared__ double sh[32 * 8];   // bsum_n<NC> needs 32 * NC
   const int l = st->l;
   const bool re = (st->flags & F_REORTH) != 0;
   for (int i = threadIdx.x; i < l; i += blockDim.x) {
@@ -543,8 +538,8 @@ k_gram_update(T* W, T* Z, int N, const T* __restrict__ w, const T* __restrict__ 
     }
     Wl[j] = a;
     Zl[j] = c;
-    nw2 += (double)(a * a);
-    wr += (double)(a * r[j]);
+    nw2 = fma((double)a, (double)a, nw2);
+    wr = fma((double)a, (double)r[j], wr);
   }
   double v[2] = {nw2, wr};
   finish_reduction<2>(v, partial, e, sh);
@@ -556,7 +551,7 @@ template <typename T>
 __global__ void __launch_bounds__(kVecThreads)
 k_rm_finish(T* W, T* Z, int N, T* x, T* r, double* partial, EpiArgs e) {
   LevelState* st = e.st;
-  __shared__ double sh[32];
+  __shared__ double sh[32 * 8];   // bsum_n<NC> needs 32 * NC
   const bool keep = !(st->flags & F_DISCARD);
   const int l = st->l;
   const T gam = (T)st->gamma, al = (T)st->alpha;
@@ -573,7 +568,7 @@ k_rm_finish(T* W, T* Z, int N, T* x, T* r, double* partial, EpiArgs e) {
       rv = fma(-al, wv, rv);
       r[j] = rv;
     }
-    r2 += (double)(rv * rv);
+    r2 = fma((double)rv, (double)rv, r2);
   }
   double v[1] = {r2};
   finish_reduction<1>(v, partial, e, sh);
@@ -582,11 +577,11 @@ k_rm_finish(T* W, T* Z, int N, T* x, T* r, double* partial, EpiArgs e) {
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads)
 k_norm(const T* __restrict__ v, int N, double* partial, EpiArgs e) {
-  __shared__ double sh[32];
+  __shared__ double sh[32 * 8];   // bsum_n<NC> needs 32 * NC
   double s = 0.0;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
     const double a = (double)v[j];
-    s += a * a;
+    s = fma(a, a, s);
   }
   double vv[1] = {s};
   finish_reduction<1>(vv, partial, e, sh);

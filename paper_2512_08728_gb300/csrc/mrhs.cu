@@ -41,7 +41,8 @@ enum : int { MF_REORTH = 1, MF_DISCARD = 2 };
 
 // Device state of one level (one MG call is active per level at any time).
 struct MState {
-  int any, any_restart, any_claim, any_reorth;   // flags the host reads (first 16 bytes)
+  int any, any_restart, any_claim, any_reorth;   // flags the host reads (first 32 bytes)
+  int nact, pad_f0, pad_f1, pad_f2;              // active columns after the last test
   int R, lcap, maxit, it;
   int iters_total, nrestart, status, guard;
   int guard_cap, level, pad0, pad1;
@@ -782,6 +783,7 @@ __global__ void k_mctl(MState* st, const MState* parent, const double* __restric
         break;
     }
   }
+  const int nact = __popc(__ballot_sync(0xffffffffu, r < R && st->act[r]));
   f_any = __any_sync(0xffffffffu, f_any);
   f_restart = __any_sync(0xffffffffu, f_restart);
   f_claim = __any_sync(0xffffffffu, f_claim);
@@ -793,6 +795,7 @@ __global__ void k_mctl(MState* st, const MState* parent, const double* __restric
         st->any = go;
         st->any_restart = go && f_restart;
         st->any_claim = f_claim;
+        st->nact = nact;
         if (go && !f_restart && !f_claim) st->guard++;
         break;
       }
@@ -875,6 +878,7 @@ struct MrhsEngine {
   int* mask = nullptr;
   MState* hst = nullptr;  // pinned host copy of the flags
   long long launches = 0;
+  std::vector<int> hist_act;   // active columns at each level-0 loop test
   std::string* err = nullptr;
   cudaStream_t s = nullptr;
   // autotuner record: per level 0 the chosen shapes and their times
@@ -1001,7 +1005,7 @@ void norms(MrhsEngine* E, const MLev& L, const double* vv) {
 }
 
 void read_flags(MrhsEngine* E, int lev) {
-  MCK(cudaMemcpyAsync(E->hst, E->lv[lev].st, 16, cudaMemcpyDeviceToHost, E->s));
+  MCK(cudaMemcpyAsync(E->hst, E->lv[lev].st, 32, cudaMemcpyDeviceToHost, E->s));
   MCK(cudaStreamSynchronize(E->s));
 }
 
@@ -1107,6 +1111,7 @@ void mg(MrhsEngine* E, int lev) {
   for (;;) {
     ctl(E, lev, CTL_TEST);
     read_flags(E, lev);
+    if (lev == 0) E->hist_act.push_back(E->hst->nact);
     if (E->hst->any_claim) { restart(E, lev, true); continue; }
     if (!E->hst->any) break;
     if (E->hst->any_restart) { restart(E, lev, false); continue; }
@@ -1385,6 +1390,7 @@ kcmg_status mrhs_solve(MrhsEngine** peng, const MrhsView& v, const double* b, do
     E->err = err;
     E->R = R;
     E->launches = 0;
+    E->hist_act.clear();
     MLev& L = E->lv[0];
     const size_t NR = (size_t)L.N * R;
     MCK(cudaMemcpyAsync(L.b, b, NR * sizeof(double), cudaMemcpyDefault, E->s));
@@ -1428,7 +1434,17 @@ kcmg_status mrhs_solve(MrhsEngine** peng, const MrhsView& v, const double* b, do
       info->res0 = res0max;
       info->rel_res = worst;
       info->kernel_launches = E->launches;
-      info->hist_len = 0;
+      // history: active columns at every level-0 loop test (type 5)
+      int m = 0;
+      if (info->hist && info->hist_type && info->hist_cap > 0) {
+        m = std::min<int>(info->hist_cap, (int)E->hist_act.size());
+        std::vector<double> hv(m);
+        std::vector<int> ht(m, 5);
+        for (int i = 0; i < m; ++i) hv[i] = E->hist_act[i];
+        MCK(cudaMemcpy(info->hist, hv.data(), m * sizeof(double), cudaMemcpyDefault));
+        MCK(cudaMemcpy(info->hist_type, ht.data(), m * sizeof(int), cudaMemcpyDefault));
+      }
+      info->hist_len = m;
     }
     if (hs[0].status != KCMG_OK) return (kcmg_status)hs[0].status;
     if (!finite) return KCMG_NONFINITE;

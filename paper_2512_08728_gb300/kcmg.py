@@ -19,6 +19,9 @@ KCMG_OK, KCMG_NOT_CONVERGED, KCMG_BREAKDOWN, KCMG_NONFINITE, KCMG_SINGULAR, \
     KCMG_INVALID_ARG, KCMG_OOM, KCMG_CUDA_ERROR = range(8)
 KCMG_FP64, KCMG_MIXED, KCMG_MIXED_BF16INV = range(3)
 PRECISIONS = {"fp64": KCMG_FP64, "mixed": KCMG_MIXED, "mixed_bf16": KCMG_MIXED_BF16INV}
+# phase kinds of the coarse-cycle kernel's timers (kcmg_kernel_report out[19 + k])
+COARSE_PHASES = ["sweep", "rm_gram1", "rm_reorth", "rm_update", "rm_finish", "transfer",
+                 "coarsest", "restart", "control"]
 
 
 class kcmg_params(C.Structure):
@@ -253,11 +256,13 @@ def kcmg_residual_noalloc(ctx, b, x, r):
 def kcmg_kernel_report(ctx, reps=0):
     """Coarse-cycle kernel counters since the last call and, with reps > 0, CUDA-event
     timings of the level-0 operator application and smoother sweep (see kcmg.h)."""
-    out = np.zeros(7 + KCMG_MAX_LEVELS)
+    out = np.zeros(7 + KCMG_MAX_LEVELS + len(COARSE_PHASES))
     _check(ctx, load_library().kcmg_kernel_report(ctx, int(reps), out.ctypes.data, out.size))
+    ph = out[7 + KCMG_MAX_LEVELS:]
     return {"coarse_launches": int(out[0]), "coarse_ms": out[1], "coarse_bytes": out[2],
             "spmv_ms": out[3], "spmv_bytes": out[4], "sweep_ms": out[5], "sweep_bytes": out[6],
-            "coarse_level_ms": out[7:].tolist()}
+            "coarse_level_ms": out[7:7 + KCMG_MAX_LEVELS].tolist(),
+            "coarse_phase_ms": dict(zip(COARSE_PHASES, ph.tolist()))}
 
 
 def _unary(name, ctx, level, x, nout, *extra):

@@ -54,6 +54,10 @@ WORKLOADS = {w.name: w for w in [
                          "nu 1:1e4, FP32 inner / FP64 refinement"),
     Workload("sipg3d_p2_64cube_rhs32", 3, 2, (64, 64, 64), 5, nrhs=32, precision="mixed",
              description="3-D SIPG p=2, 64^3 cells, 32 right-hand sides in one solve"),
+    Workload("sipg3d_p2_32cube_rhs32", 3, 2, (32, 32, 32), 4, nrhs=32, precision="mixed_bf16",
+             description="3-D SIPG p=2, 32^3 cells (327,680 DOFs), nu 1:1000, 32 right-hand "
+                         "sides in one solve (the 32-column batch at a size whose slowest "
+                         "column converges within a minute)"),
     Workload("sipg3d_p2_32cube_lognormal", 3, 2, (32, 32, 32), 4, nu_kind="lognormal",
              description="3-D SIPG p=2, 32^3 cells (327,680 DOFs), log nu ~ N(0,1) + ln 1000 "
                          "inside the ball; adjoint gradient workload"),

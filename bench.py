@@ -171,10 +171,13 @@ def run_mrhs(pkg, rank, dev, stream, hbm_peak, args):
     import torch
 
     from workloads import workload
-    pm = workload(MRHS_WORKLOAD).make(rank)
+    wname = args.mrhs_workload or MRHS_WORKLOAD
+    prec_m = args.mrhs_precision or MRHS_PRECISION
+    lmax_m = args.mrhs_lmax if args.mrhs_lmax is not None else MRHS_LMAX
+    pm = workload(wname).make(rank)
     B = torch.from_numpy(pm.b).to(dev)
     X = torch.zeros_like(B)
-    sm = pkg.KCycleSolver(pm, precision=MRHS_PRECISION, lmax=MRHS_LMAX, stream=stream.cuda_stream)
+    sm = pkg.KCycleSolver(pm, precision=prec_m, lmax=lmax_m, stream=stream.cuda_stream)
     pkg.kcmg_solve(sm.ctx, B, X, RTOL, 0.0, 1)   # build the batched engine and autotune
     tune = sm.mrhs_tuning()
     X.zero_()
@@ -188,7 +191,7 @@ def run_mrhs(pkg, rank, dev, stream, hbm_peak, args):
     # the same operator solved one column at a time (columns 0 and 1, FP64 and the same
     # mixed form) for comparison
     single = {}
-    for prec in ("fp64", MRHS_PRECISION):
+    for prec in (() if args.no_single else ("fp64", prec_m)):
         s1 = pkg.KCycleSolver(pm, precision=prec, use_graph=True, lmax=200, stream=stream.cuda_stream)
         ts = []
         for j in (0, 1):
@@ -209,7 +212,7 @@ def run_mrhs(pkg, rank, dev, stream, hbm_peak, args):
     R = int(pm.b.shape[1])
     C = pm.ndof // pm.np_
     np2, S = pm.np_ * pm.np_, 2 * pm.d + 1
-    inv_b = 2 if MRHS_PRECISION == "mixed_bf16" else 4
+    inv_b = 2 if prec_m == "mixed_bf16" else 4
     # algorithmic bytes of one tensor-core sweep (sweeps 2..5): FP32 off-diagonal blocks,
     # stored inverses, r (FP32) and the old and new iterates (FP32), each once
     sweep_bytes = C * ((S - 1) * np2 * 4 + np2 * inv_b) + 3 * pm.ndof * R * 4
@@ -217,13 +220,15 @@ def run_mrhs(pkg, rank, dev, stream, hbm_peak, args):
     # FP64 block SpMM: one FMA per block element and column
     spmm_tflops = 2.0 * S * np2 * C * R / (tune["spmm_ms"] * 1e-3) / 1e12 if tune["spmm_ms"] > 0 else 0.0
     return {
-        "value": pm.ndof * R / (mms * 1e-3), "unit": UNIT, "workload": MRHS_WORKLOAD, "nrhs": R,
+        "value": pm.ndof * R / (mms * 1e-3), "unit": UNIT, "workload": wname, "nrhs": R,
         "ms_per_step": mms, "status": inf["status"], "rel_res": inf["rel_res"],
         "cycles": inf["iters"], "level_iters": inf["level_iters"][:pm.nlevels],
-        "lmax": MRHS_LMAX, "kernel_launches": inf["kernel_launches"],
+        "lmax": lmax_m, "precision": prec_m, "kernel_launches": inf["kernel_launches"],
         "single_column_solves": single,
-        "dtype": "tensor-core TF32x3 smoother sweeps (FP32 accumulation), BF16 block inverses; "
-                 "f64 residual minimisation, transfers, coarsest solve",
+        "dtype": ("tensor-core TF32x3 smoother sweeps (FP32 accumulation)"
+                  + (", BF16 block inverses" if prec_m == "mixed_bf16" else "")
+                  + "; f64 residual minimisation, transfers, coarsest solve")
+                 if prec_m != "fp64" else "f64",
         "autotuner": tune,
         "sweep_tc": {"bound": "hbm", "achieved": sweep_gbs, "peak": hbm_peak, "unit": "GB/s",
                      "frac": sweep_gbs / hbm_peak, "bytes_per_launch": sweep_bytes,
@@ -243,6 +248,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mrhs-only", action="store_true",
+                    help="run only the batched form (profiling runs): skips the single-RHS solves")
+    ap.add_argument("--mrhs-workload", default=None,
+                    help="batched workload name (default %s)" % "sipg3d_p2_32cube_rhs32")
+    ap.add_argument("--mrhs-precision", default=None, help="batched form precision (default mixed_bf16)")
+    ap.add_argument("--mrhs-lmax", type=int, default=None, help="batched level-0 basis length")
+    ap.add_argument("--no-single", action="store_true",
+                    help="batched form: skip the single-column comparison solves")
     ap.add_argument("--mrhs", action="store_true",
                     help="also solve a 32-right-hand-side batch (32^3 p=2, 32 columns of U[-1,1]) "
                          "in the batched mixed form, with single-column solves of the same "
@@ -275,8 +288,13 @@ def main():
     pkg.build()
     hbm_peak, peak_kind = _peaks()
 
-    pr = workload(args.workload).make(rank)
     stream = torch.cuda.current_stream()
+    if args.mrhs_only:
+        out = run_mrhs(pkg, rank, dev, stream, hbm_peak, args)
+        if rank == 0:
+            print(json.dumps({"mrhs": out}), flush=True)
+        return
+    pr = workload(args.workload).make(rank)
     s = pkg.KCycleSolver(pr, precision="fp64", use_graph=not args.eager, lmax=LMAX,
                          stream=stream.cuda_stream)
     b = torch.from_numpy(pr.b).to(dev)
@@ -323,11 +341,16 @@ def main():
     coarse_bytes = rep["coarse_bytes"] / cl
     coarse_gbs = coarse_bytes / (coarse_ms * 1e-3) / 1e9 if coarse_ms > 0 else 0.0
     share = rep["coarse_ms"] / ms if ms > 0 else 0.0
-    fp64_gbs = FP64_TFLOPS * 1e12 / 2 * 8 / 1e9
+    fp64_gbs = FP64_TFLOPS * 1e12 / 2 * 8 / 1e9   # operator bytes/s at the FP64 FMA peak
+    # The coarse cycle's data (operators of 41K and 5K rows, their bases) stays in the
+    # 129 MB L2: ncu measures ~1% of its algorithmic bytes as DRAM traffic, so HBM does not
+    # bound it.  Its arithmetic is FP64 (one FMA per 8-byte operator element), and the
+    # binding roofline is the FP64 FMA rate, expressed as operator bytes per second.
     kernels = [
-        {"name": "k_coarse_cycle (levels 1-4, persistent)", "bound": "hbm",
-         "achieved": coarse_gbs, "peak": hbm_peak, "unit": "GB/s",
-         "frac": coarse_gbs / hbm_peak, "ms_per_launch": coarse_ms,
+        {"name": "k_coarse_cycle (levels 2-4 at 64^3, persistent)", "bound": "alu",
+         "achieved": coarse_gbs, "peak": fp64_gbs, "unit": "GB/s",
+         "frac": coarse_gbs / fp64_gbs, "hbm_frac": coarse_gbs / hbm_peak,
+         "ms_per_launch": coarse_ms,
          "bytes_per_launch": coarse_bytes, "share_of_step": share,
          "ms_per_launch_by_level": [v / cl for v in rep["coarse_level_ms"][:pr.nlevels]],
          "ms_per_launch_by_phase": {k: v / cl for k, v in rep["coarse_phase_ms"].items()}},
@@ -411,8 +434,10 @@ def main():
                        "l2": "inputs larger than L2 (operator 1.47 GB vs 129 MB L2): no flush"},
             "status": status, "rel_res": rel, "cycles": cycles, "level_iters": lvl[:pr.nlevels],
             "roofline": {"bound": kernels[0]["bound"], "achieved": kernels[0]["achieved"],
-                         "peak": hbm_peak, "unit": "GB/s", "frac": kernels[0]["frac"],
-                         "traffic": None, "peak_kind": peak_kind,
+                         "peak": kernels[0]["peak"], "unit": "GB/s", "frac": kernels[0]["frac"],
+                         "traffic": None,
+                         "peak_kind": "measured FP64 FMA rate (1.198 TFLOP/s, profiles/fp64_alu_peak_gb300.md) "
+                                      "as operator bytes/s; HBM peak " + f"{hbm_peak} GB/s ({peak_kind})",
                          "kernel": kernels[0]["name"]},
             "kernels": kernels,
             "forms": forms,

@@ -17,6 +17,12 @@
  *               next level, prolongate, RM, post-smoother, RM.
  *   smooth      Alg. BJ (block Jacobi) started from x = 0 with a fixed sweep count:
  *               r = b - A x; x_i += omega A_ii^{-1} r_i for every cell block i.
+ *   async_mg0   Alg. AsyncMG (task-parallel OrthoMG) on level 0, with the smoother group's
+ *               loop run a fixed number m of times per cycle so that the result does not
+ *               depend on timing: per cycle the coarse path restricts the residual of the
+ *               cycle start, solves the coarse problem (recursive MG, or directly) and
+ *               prolongates; the smoother path applies m smoother + RM steps to the
+ *               current residual meanwhile; then one RM with the coarse correction.
  *   criteria    Sec. 4.2 (convergence criteria): level 0 the user tolerance; level 1
  *               ||r|| <= 0.1 ||r0|| or 20 iterations; level 2 ||r|| <= 0.5 ||r0|| or 2
  *               iterations; deeper levels one iteration per visit; the last level of the
@@ -74,6 +80,7 @@ typedef struct {
     int level_iters[ORC_MAXLEV];
     int breakdowns_in_row, status_flag;
     int lmax, restarts;
+    int async_m;     /* 0: Alg. 2 on level 0; m > 0: Alg. AsyncMG with m smoother steps */
     double res0;     /* ||b - A x0|| of the top-level solve */
 } osolver;
 
@@ -428,6 +435,56 @@ static void mg(osolver *S, int lev, const double *b, double *x, double rtol0, do
     memcpy(x, L->x, sizeof(double) * N);
 }
 
+/* Alg. AsyncMG on level 0 (async_m smoother steps per cycle); x: in x0, out x.  The
+   stopping test, the level-0 confirmation restart and the lmax restart (now when the
+   basis could not take one more cycle's async_m + 1 corrections) are those of mg. */
+static void async_mg0(osolver *S, const double *b, double *x, double rtol0, double atol0,
+                      int maxit0) {
+    olevel *L = &S->lv[0];
+    olevel *C = &S->lv[1];
+    int N = ndof(S, 0);
+    const int per_cycle = S->async_m + 1;
+    L->l = 0;                                                 /* Z := {}, W := {} */
+    apply(S, 0, x, L->r0);                                    /* r0 := b - A x0 */
+    for (int k = 0; k < N; k++) { L->r0[k] = b[k] - L->r0[k]; L->r[k] = L->r0[k]; L->x0[k] = x[k]; L->x[k] = x[k]; }
+    double n0 = sqrt(dot(N, L->r0, L->r0));
+    S->res0 = n0;
+    double eps = fmax(rtol0 * n0, atol0);
+    record(S, 0, 0);
+    double *zc = malloc(sizeof(double) * N);
+    int it = 0;
+    for (;;) {
+        if (!(sqrt(dot(N, L->r, L->r)) > eps)) {
+            if (L->l == 0) break;                             /* confirm on b - A x */
+            restart(S, 0, b);
+            if (!(sqrt(dot(N, L->r, L->r)) > eps)) break;
+        }
+        if (it >= maxit0 || S->status_flag != ORC_OK) break;
+        /* coarse group: works on the residual of the cycle start */
+        restrict_(S, 0, L->r, C->bc);                         /* r_c := R r */
+        if (S->nlev == 2) {
+            coarse_solve(S, C->bc, C->xc);                    /* z_c := A_c \ r_c */
+        } else {
+            memset(C->xc, 0, sizeof(double) * ndof(S, 1));
+            mg(S, 1, C->bc, C->xc, 0, 0, 0);                  /* z_c := MG(A_c, r_c, 0) */
+        }
+        prolong(S, 0, C->xc, zc);                             /* z_cor := P z_c */
+        /* smoother group: m smoothing + RM steps on the current residual */
+        for (int k = 0; k < S->async_m; k++) {
+            smooth(S, 0, L->r, L->z);
+            mg_rm(S, 0, b, L->z, 1);
+        }
+        /* the synchronisation: RM with the coarse correction */
+        memcpy(L->z, zc, sizeof(double) * N);
+        mg_rm(S, 0, b, L->z, 2);
+        it++;
+        S->level_iters[0]++;
+        if (S->lmax > 0 && L->l + per_cycle > S->lmax) restart(S, 0, b);
+    }
+    free(zc);
+    memcpy(x, L->x, sizeof(double) * N);
+}
+
 /* ------------------------------------------------------------------------ C interface */
 void orc_destroy(void *h);
 
@@ -511,7 +568,8 @@ int orc_solve(void *h, const double *b, double *x, double rtol, double atol, int
     S->hist = hist; S->hist_type = hist_type; S->hist_cap = hist ? hist_cap : 0; S->hist_len = 0;
     memset(S->level_iters, 0, sizeof(S->level_iters));
     S->breakdowns_in_row = 0; S->status_flag = ORC_OK; S->restarts = 0;
-    mg(S, 0, b, x, rtol, atol, maxiter);
+    if (S->async_m > 0) async_mg0(S, b, x, rtol, atol, maxiter);
+    else mg(S, 0, b, x, rtol, atol, maxiter);
     olevel *L = &S->lv[0];
     apply(S, 0, x, L->t);                                     /* report the true residual */
     for (int k = 0; k < N; k++) L->t[k] = b[k] - L->t[k];
@@ -625,3 +683,5 @@ void orc_grad_lognu(int dim, int np, const int *n, const double *nu, const doubl
 /* number of stored basis vectors on level lev (after a solve: of its last MG call) */
 int orc_basis_size(void *h, int lev) { return ((osolver *)h)->lv[lev].l; }
 int orc_restarts(void *h) { return ((osolver *)h)->restarts; }
+/* m > 0: level 0 runs Alg. AsyncMG with m smoother steps per cycle; 0: Alg. 2 */
+void orc_set_async(void *h, int m) { ((osolver *)h)->async_m = m > 0 ? m : 0; }

@@ -56,6 +56,7 @@ def _load():
             lib.orc_rm_basis.argtypes = [C.c_void_p, C.c_int, _dp, _dp]
             lib.orc_restarts.restype = C.c_int
             lib.orc_restarts.argtypes = [C.c_void_p]
+            lib.orc_set_async.argtypes = [C.c_void_p, C.c_int]
             lib.orc_basis_size.restype = C.c_int
             lib.orc_basis_size.argtypes = [C.c_void_p, C.c_int]
             lib.orc_grad_lognu.argtypes = [C.c_int, C.c_int, _ip, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
@@ -83,7 +84,7 @@ class OracleSolver:
     """FP64 CPU K-cycle OrthoMG on a Cartesian block-ELL operator and its hierarchy."""
 
     def __init__(self, dim, np_, n, nlevels, blocks, prolong, omega=0.7, sweeps=5,
-                 lvl_rtol=None, lvl_maxit=None, lmax=0, transpose=False):
+                 lvl_rtol=None, lvl_maxit=None, lmax=0, transpose=False, async_smooth=0):
         self._lib = _load()
         rt, mi = default_level_criteria(nlevels)
         if lvl_rtol is not None:
@@ -101,6 +102,8 @@ class OracleSolver:
         self.status = st.value
         if not self._h:
             raise RuntimeError(f"oracle setup failed with status {st.value}")
+        # level 0 as Alg. AsyncMG with async_smooth smoother steps per cycle (0: Alg. 2)
+        self._lib.orc_set_async(self._h, int(async_smooth))
 
     @classmethod
     def from_problem(cls, pr, **kw):

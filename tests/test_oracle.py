@@ -299,3 +299,92 @@ def test_adjoint_gradient_matches_central_differences(d, p, n):
         e[K] = hstep
         fd[K] = (_loss_and_solution(pr, lognu + e, ut)[0] - _loss_and_solution(pr, lognu - e, ut)[0]) / (2 * hstep)
     assert np.abs(g - fd).max() <= 1e-6 * np.abs(fd).max()
+
+
+# ------------------------------------------------------------------ Alg. AsyncMG (task-parallel)
+def _dense_prolongation(pr):
+    """P (N0 x N1) of a 2^d agglomeration from the child matrices P_k (input data)."""
+    n0 = np.array(pr.n)
+    n1 = n0 // 2
+    d, Np = pr.d, pr.np_
+    C0, C1 = int(np.prod(n0)), int(np.prod(n1))
+    P = np.zeros((C0 * Np, C1 * Np))
+    for K in range(C0):
+        c = np.unravel_index(K, tuple(n0[::-1]))[::-1]          # x fastest
+        J = np.ravel_multi_index(tuple((np.array(c) // 2)[::-1]), tuple(n1[::-1]))
+        k = sum(((c[j] & 1) << j) for j in range(d))
+        P[K * Np:(K + 1) * Np, J * Np:(J + 1) * Np] = pr.prolong[k]
+    return P
+
+
+def _dense_bj(A, Np, r, omega, sweeps):
+    """Alg. BJ from z = 0 with dense algebra: z += omega D^-1 (r - A z)."""
+    N = A.shape[0]
+    Dinv = np.zeros_like(A)
+    for K in range(N // Np):
+        s = slice(K * Np, (K + 1) * Np)
+        Dinv[s, s] = np.linalg.inv(A[s, s])
+    z = np.zeros(N)
+    for _ in range(sweeps):
+        z = z + omega * Dinv @ (r - A @ z)
+    return z
+
+
+@pytest.mark.parametrize("m", [1, 2, 3])
+def test_async_first_cycle_is_least_squares_over_its_corrections(m):
+    """One cycle of Alg. AsyncMG on two levels.  The coarse correction is
+    z_cor = P A_c^-1 P^T r0, from the cycle-start residual.  The smoother corrections are
+    z_k = BJ(r_{k-1}), each from the residual the previous minimisation left.  By Alg. 1,
+    the residual after the cycle is the least-squares residual of r0 over
+    A span{z_1..z_m, z_cor}.  Everything here is rebuilt with dense algebra."""
+    pr = make_problem(2, 1, (8, 8), 2, seed=11)
+    A = dense_matrix(pr.blocks, pr.nbr)
+    P = _dense_prolongation(pr)
+    Ac = P.T @ A @ P
+    r0 = pr.b.copy()
+    zc = P @ np.linalg.solve(Ac, P.T @ r0)
+    Zs, r = [], r0.copy()
+    for _ in range(m):
+        z = _dense_bj(A, pr.np_, r, 0.7, 5)
+        Zs.append(z)
+        Q, _ = np.linalg.qr(A @ np.stack(Zs, axis=1))
+        r = r0 - Q @ (Q.T @ r0)
+    Q, _ = np.linalg.qr(A @ np.stack(Zs + [zc], axis=1))
+    r_expected = np.linalg.norm(r0 - Q @ (Q.T @ r0))
+    S = _solver(pr, async_smooth=m)
+    x, info = S.solve(pr.b, rtol=1e-14, maxiter=1)
+    h, t = info["hist"], info["hist_type"]
+    assert list(t[:m + 2]) == [0] + [1] * m + [2]
+    assert abs(h[m + 1] - r_expected) <= 1e-10 * h[0]
+    # and the iterate's true residual is that residual
+    assert abs(np.linalg.norm(pr.b - A @ x) - r_expected) <= 1e-10 * h[0]
+
+
+@pytest.mark.parametrize("name", ["sipg2d_p1_16x16", "sipg3d_p1_8x4x4", "sipg2d_p2_32x16",
+                                  "sipg3d_p2_8cube"])
+@pytest.mark.parametrize("m", [1, 3])
+def test_async_solution_matches_dense_lu(name, m):
+    pr = workload(name).make(0)
+    A = dense_matrix(pr.blocks, pr.nbr)
+    xs = np.linalg.solve(A, pr.b)
+    x, info = _solver(pr, async_smooth=m).solve(pr.b, rtol=1e-10, maxiter=2000)
+    assert info["status"] == ORC_OK
+    assert np.linalg.norm(pr.b - A @ x) <= 1e-10 * np.linalg.norm(pr.b)
+    assert np.linalg.norm(x - xs) <= 1e-8 * np.linalg.norm(xs)
+    h, t = info["hist"], info["hist_type"]
+    d = np.diff(h)
+    assert np.all(d[t[1:] != 4] <= 1e-13 * h[0])      # Alg. 1: monotone within runs
+
+
+def test_async_restart_keeps_basis_within_lmax():
+    """With lmax = 8 and m = 3 (4 corrections per cycle) the level restarts before the
+    basis would exceed 8 vectors; the solve still converges."""
+    pr = workload("sipg2d_p1_16x16").make(1)
+    S = _solver(pr, async_smooth=3, lmax=8)
+    x, info = S.solve(pr.b, rtol=1e-10, maxiter=2000)
+    assert info["status"] == ORC_OK and info["restarts"] >= 1
+    assert S.basis_size(0) <= 8
+    t = info["hist_type"]
+    # between two restart entries (type 4) there are at most two cycles' corrections
+    runs = np.split(t, np.where(t == 4)[0])
+    assert max(int(np.sum(r != 4) - np.sum(r == 0)) for r in runs) <= 8

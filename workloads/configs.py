@@ -58,6 +58,9 @@ WORKLOADS = {w.name: w for w in [
              description="3-D SIPG p=2, 32^3 cells (327,680 DOFs), nu 1:1000, 32 right-hand "
                          "sides in one solve (the 32-column batch at a size whose slowest "
                          "column converges within a minute)"),
+    Workload("sipg3d_p2_48cube_rhs32", 3, 2, (48, 48, 48), 4, nrhs=32, precision="mixed_bf16",
+             description="3-D SIPG p=2, 48^3 cells, 32 right-hand sides (profiling case of the "
+                         "batched kernels: vectors larger than L2, a few GB on the device)"),
     Workload("sipg3d_p2_32cube_lognormal", 3, 2, (32, 32, 32), 4, nu_kind="lognormal",
              description="3-D SIPG p=2, 32^3 cells (327,680 DOFs), log nu ~ N(0,1) + ln 1000 "
                          "inside the ball; adjoint gradient workload"),

@@ -92,6 +92,14 @@ typedef struct {
                                 three TF32 products (head*head + head*tail + tail*head,
                                 FP32-level accuracy); 1 = a single TF32 product (about 2^-11
                                 relative per product; can stall the coarse levels) */
+    int async_smooth;        /* 0: level 0 runs Alg. 2 (multiplicative K-cycle).  m > 0:
+                                level 0 runs the task-parallel cycle of Alg. AsyncMG with
+                                a fixed m: the coarse path (restriction of the cycle-start
+                                residual, MG on level 1, prolongation) runs on a second
+                                stream while the smoother path applies m smoother + RM
+                                steps; one RM with the coarse correction closes the cycle.
+                                The level restarts when its basis could not take one more
+                                cycle (m + 1 vectors).  Single right-hand side only. */
 } kcmg_params;
 
 /* Fill p with the defaults of Sec. 4.2 / Alg. BJ for the given sizes (blocks, prolong

@@ -47,6 +47,8 @@ struct kcmg_ctx {
   cudaStream_t user = nullptr, s = nullptr;
   cudaStream_t cap[KCMG_MAX_LEVELS + 2] = {};
   cudaEvent_t ev = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;   // task-parallel level-0 cycle
+  double* zc = nullptr;                               // its coarse correction (level 0)
   std::vector<Level> lv;
   double* P64 = nullptr;
   float* P32 = nullptr;
@@ -408,22 +410,91 @@ struct Cycle {
                      epi(lev, EPI_RESTART), 1, s);
   }
 
+  // One cycle of Alg. AsyncMG on level 0 with a fixed smoother count m.  The coarse path
+  // (restriction of the cycle-start residual, MG on level 1 or the direct solve,
+  // prolongation into zc) runs on its own stream, forked after the restriction; the
+  // smoother path applies m smoother + RM steps on s meanwhile; after the join one RM
+  // with zc closes the cycle.  The two paths share no buffer: the smoother path writes the
+  // level-0 z, t, w, W, Z, x, r and state, the coarse path level >= 1 buffers and zc.
+  template <typename V>
+  void body_async(const V* Aop, cudaStream_t s) {
+    Level& L = ctx->lv[0];
+    Level& C = ctx->lv[1];
+    cudaStream_t cs = ctx->cap[KCMG_MAX_LEVELS + 1];
+    const bool direct = ctx->nlev == 2;
+    const bool persistent = !direct && ctx->coarse_kernel && ctx->cc_lev0 == 1;
+    if (!direct && !persistent && capture) {
+      cudaGraph_t g;
+      cudaStreamCaptureStatus cst;
+      const cudaGraphNode_t* deps;
+      const cudaGraphEdgeData* ed;
+      size_t nd;
+      unsigned long long id;
+      CK(cudaStreamGetCaptureInfo(s, &cst, &id, &g, &deps, &ed, &nd));
+      CK(cudaGraphConditionalHandleCreate(&handle[1], g, 0, 0));
+    }
+    launches += 1;                                                      // r_c = R r
+    if (direct)
+      launch_restrict<V, V>(ctx->np, ctx->dim, L.n, C.n, ctx->P64, static_cast<V*>(L.r),
+                            static_cast<V*>(C.b), nullptr, nullptr, nullptr, EpiArgs{}, s);
+    else if (persistent)
+      launch_restrict<V, V>(ctx->np, ctx->dim, L.n, C.n, ctx->P64, static_cast<V*>(L.r),
+                            static_cast<V*>(C.b), static_cast<V*>(C.r), static_cast<V*>(C.x),
+                            nullptr, EpiArgs{}, s);
+    else
+      launch_restrict<V, V>(ctx->np, ctx->dim, L.n, C.n, ctx->P64, static_cast<V*>(L.r),
+                            static_cast<V*>(C.b), static_cast<V*>(C.r), static_cast<V*>(C.x),
+                            C.partial, epi(1, EPI_MG_BEGIN), s);
+    CK(cudaEventRecord(ctx->fork_ev, s));                                // fork
+    CK(cudaStreamWaitEvent(cs, ctx->fork_ev, 0));
+    // smoother path first, so that host-driven coarse control overlaps it
+    for (int k = 0; k < ctx->p.async_smooth; ++k) {
+      V* z = smooth<V>(0, static_cast<V*>(L.r), s);
+      rm<V>(0, Aop, z, 0, 1, s);
+    }
+    // coarse path
+    if (direct) {
+      launches += 1;
+      launch_coarse_gemv<V>(ctx->Ainv, ctx->Nc, static_cast<V*>(C.b), static_cast<V*>(C.x), cs);
+    } else if (persistent) {
+      launches += 1;
+      launch_coarse(ctx, cs);
+    } else {
+      loop<V>(1, (const V*)C.A64, cs);
+    }
+    launches += 1;
+    launch_prolong<V, V>(ctx->np, ctx->dim, L.n, C.n, ctx->P64, static_cast<V*>(C.x),
+                         reinterpret_cast<V*>(ctx->zc), cs);                // z_cor = P z_c
+    CK(cudaEventRecord(ctx->join_ev, cs));                               // join
+    CK(cudaStreamWaitEvent(s, ctx->join_ev, 0));
+    rm<V>(0, Aop, reinterpret_cast<const V*>(ctx->zc), 1, 2, s);
+    launches += 1;                                                       // restart check
+    launch_residual_dd(ctx->np, ctx->dim, (const double*)Aop, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
+                       (const double*)L.x, (double*)L.r, (const double*)L.b, L.partial,
+                       epi(0, EPI_RESTART), 1, s);
+  }
+
   long long body_launches = 0;                        // level-0 loop body (capture)
   long long body_kernels[KCMG_MAX_LEVELS] = {};       // kernels of one body per level,
   long long loop_total[KCMG_MAX_LEVELS + 1] = {};     // excluding nested loops
 
-  bool read_cond(int lev) {
+  // host-driven control: the loop condition, read on the stream that runs the level
+  bool read_cond(int lev, cudaStream_t s) {
     int c = 0;
-    CK(cudaMemcpyAsync(&c, &ctx->lv[lev].st->cond, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
-    CK(cudaStreamSynchronize(ctx->s));
+    CK(cudaMemcpyAsync(&c, &ctx->lv[lev].st->cond, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
     return c != 0;
   }
 
   // while (cond_lev) body(lev): host-driven, or a conditional while node when capturing
   template <typename V>
   void loop(int lev, const V* Aop, cudaStream_t s) {
+    const bool task_parallel = lev == 0 && ctx->p.async_smooth > 0;
     if (!capture) {
-      while (read_cond(lev)) body<V>(lev, Aop, s);
+      while (read_cond(lev, s)) {
+        if (task_parallel) body_async<V>(Aop, s);
+        else body<V>(lev, Aop, s);
+      }
       return;
     }
     cudaGraph_t g;
@@ -446,7 +517,8 @@ struct Cycle {
                                      cudaStreamCaptureModeRelaxed));
     const long long before = launches;
     loop_total[lev + 1] = 0;
-    body<V>(lev, Aop, bs);
+    if (task_parallel) body_async<V>(Aop, bs);
+    else body<V>(lev, Aop, bs);
     loop_total[lev] = launches - before;
     body_kernels[lev] = loop_total[lev] - loop_total[lev + 1];
     if (lev == 0) body_launches = launches - before;
@@ -498,6 +570,7 @@ void init_states(kcmg_ctx* ctx, double rtol0, double atol0, int maxit0) {
     h.brk = 1e-14;
     h.guard = 0;
     h.guard_cap = (int)cap;
+    h.per_cycle = (l == 0 && ctx->p.async_smooth > 0) ? ctx->p.async_smooth + 1 : 3;
     if (!ctx->lv[l].st) continue;   // the coarsest level is solved directly: no state
     CK(cudaMemcpyAsync(ctx->lv[l].st, &h, sizeof h, cudaMemcpyHostToDevice, ctx->s));
   }
@@ -725,6 +798,8 @@ void kcmg_destroy(kcmg_ctx* ctx) {
   for (auto& c : ctx->cap) if (c) cudaStreamDestroy(c);
   if (ctx->s) cudaStreamDestroy(ctx->s);
   if (ctx->ev) cudaEventDestroy(ctx->ev);
+  if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
   delete ctx;
 }
 
@@ -758,6 +833,7 @@ kcmg_ctx* build_ctx(const kcmg_params* p, cudaStream_t user, const double* block
       REQUIRE(p->n[j] > 0 && p->n[j] % (1 << (p->nlevels - 1)) == 0,
               "n[%d] = %d is not divisible by 2^(nlevels-1)", j, p->n[j]);
     REQUIRE(p->lmax >= 0 && p->lmax <= kLcapMax - 3, "lmax must be in [0, %d]", kLcapMax - 3);
+    REQUIRE(p->async_smooth >= 0 && p->async_smooth <= 64, "async_smooth must be in [0, 64]");
     ctx->dim = p->dim;
     ctx->np = p->np;
     ctx->S = 2 * p->dim + 1;
@@ -768,8 +844,16 @@ kcmg_ctx* build_ctx(const kcmg_params* p, cudaStream_t user, const double* block
     int dev = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaStreamCreateWithFlags(&ctx->s, cudaStreamNonBlocking));
-    for (int l = 0; l < KCMG_MAX_LEVELS + 2; ++l) CK(cudaStreamCreateWithFlags(&ctx->cap[l], cudaStreamNonBlocking));
+    for (int l = 0; l < KCMG_MAX_LEVELS + 1; ++l) CK(cudaStreamCreateWithFlags(&ctx->cap[l], cudaStreamNonBlocking));
+    {  // the coarse path of the task-parallel cycle (eager form): highest priority, so
+       // that its latency-bound kernels get SMs first while the smoother path fills the rest
+      int lo = 0, hi = 0;
+      CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+      CK(cudaStreamCreateWithPriority(&ctx->cap[KCMG_MAX_LEVELS + 1], cudaStreamNonBlocking, hi));
+    }
     CK(cudaEventCreateWithFlags(&ctx->ev, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming));
     if (user) {
       CK(cudaEventRecord(ctx->ev, user));
       CK(cudaStreamWaitEvent(ctx->s, ctx->ev, 0));
@@ -900,6 +984,7 @@ kcmg_ctx* build_ctx(const kcmg_params* p, cudaStream_t user, const double* block
     }
     const size_t N0 = ctx->lv[0].N;
     ctx->ro = dalloc<double>(ctx, N0);
+    if (p->async_smooth > 0) ctx->zc = dalloc<double>(ctx, N0);
     ctx->hist = dalloc<double>(ctx, ctx->hist_cap);
     ctx->hist_type = dalloc<int>(ctx, ctx->hist_cap);
     size_t maxN = 0;

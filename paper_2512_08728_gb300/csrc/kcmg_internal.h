@@ -38,6 +38,7 @@ struct LevelState {
   int nrestart;
   int hist_len, hist_cap;
   int guard, guard_cap; // loop bodies executed on this level in this solve, and their cap
+  int per_cycle;        // corrections appended per cycle (restart when l + per_cycle > cap)
   unsigned int ticket;  // last-block counter of the reduction kernels
   double rnorm, rnorm0, eps, rtol, atol;
   double naz2;      // ||A z||^2 of the RM call in flight

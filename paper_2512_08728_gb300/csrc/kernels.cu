@@ -154,7 +154,7 @@ __device__ void epilogue(const EpiArgs& e, const double* sums) {
         st->iters_total++;
         const int cap = (st->lmax > 0 && st->lmax < st->lcap) ? st->lmax : st->lcap;
         if (st->level == 0 && !(st->rnorm > st->eps) && st->l > 0) st->restart_req = 1;
-        if (st->l + 3 > cap) st->restart_req = 1;
+        if (st->l + st->per_cycle > cap) st->restart_req = 1;
       }
     } break;
     case EPI_RESTART: {

@@ -30,7 +30,7 @@ class kcmg_params(C.Structure):
                 ("sweeps", C.c_int), ("lvl_rtol", C.c_double * KCMG_MAX_LEVELS),
                 ("lvl_maxit", C.c_int * KCMG_MAX_LEVELS), ("lmax", C.c_int),
                 ("precision", C.c_int), ("use_graph", C.c_int), ("coarse_persistent", C.c_int),
-                ("tc_tf32_only", C.c_int)]
+                ("tc_tf32_only", C.c_int), ("async_smooth", C.c_int)]
 
 
 class kcmg_info(C.Structure):
@@ -331,7 +331,7 @@ class KCycleSolver:
 
     def __init__(self, problem, precision="fp64", use_graph=True, omega=0.7, sweeps=5,
                  lmax=0, lvl_rtol=None, lvl_maxit=None, coarse_persistent=True, stream=None,
-                 tc_tf32_only=0):
+                 tc_tf32_only=0, async_smooth=0):
         pr = problem
         self.dim, self.np_, self.nlevels = pr.d, pr.np_, pr.nlevels
         self.ndof = pr.ndof
@@ -341,6 +341,7 @@ class KCycleSolver:
         p.use_graph = int(use_graph)
         p.coarse_persistent = int(coarse_persistent)
         p.tc_tf32_only = int(tc_tf32_only)
+        p.async_smooth = int(async_smooth)
         if lvl_rtol is not None:
             for i, v in enumerate(lvl_rtol):
                 p.lvl_rtol[i] = v

@@ -267,3 +267,61 @@ def test_gradient_kernel_matches_oracle():
     g = s.grad_lognu(pr.nu, pr.ref, lam, u)
     s.close()
     assert _rel(g, grad_lognu(pr, pr.nu, lam, u)) < 1e-12
+
+
+# ------------------------------------------------------------------ Alg. AsyncMG on the GPU
+@pytest.mark.parametrize("name", SMALL + ["ragged_3d_p2", "sipg2d_p1_32x32_5lev"])
+@pytest.mark.parametrize("m", [1, 3])
+@pytest.mark.parametrize("use_graph,persistent", [(False, False), (True, False), (True, True)])
+def test_task_parallel_cycle_matches_oracle(name, m, use_graph, persistent):
+    """Level 0 as Alg. AsyncMG with m smoother steps per cycle; the coarse path runs on a
+    second stream.  The solution must match the oracle's AsyncMG solve."""
+    pr = _problem(name)
+    x_or, info_or = OracleSolver.from_problem(pr, async_smooth=m).solve(pr.b, rtol=1e-10, maxiter=2000)
+    assert info_or["status"] == 0
+    s = pkg.KCycleSolver(pr, precision="fp64", use_graph=use_graph, coarse_persistent=persistent,
+                         async_smooth=m)
+    x, info = s.solve(pr.b, rtol=1e-10, maxiter=2000)
+    s.close()
+    assert info["status"] == 0, info
+    _check_solution(pr, x, info, x_or)
+
+
+@pytest.mark.parametrize("m", [1, 2, 4])
+@pytest.mark.parametrize("persistent", [False, True])
+def test_task_parallel_first_cycles_follow_the_oracle(m, persistent):
+    """The residual history of the first cycles (m smoother RMs, then the coarse RM from
+    the cycle-start residual) agrees with the oracle's, entry by entry."""
+    pr = make_problem(3, 2, (8, 8, 8), 3, seed=9)
+    _, io = OracleSolver.from_problem(pr, async_smooth=m).solve(pr.b, rtol=1e-14, maxiter=3)
+    s = pkg.KCycleSolver(pr, precision="fp64", use_graph=True, coarse_persistent=persistent,
+                         async_smooth=m)
+    _, info = s.solve(pr.b, rtol=1e-14, maxiter=3)
+    s.close()
+    n = 1 + 3 * (m + 1)
+    assert list(info["hist_type"][:n]) == list(io["hist_type"][:n])
+    assert list(info["hist_type"][1:m + 2]) == [1] * m + [2]
+    h, ho = info["hist"][:n], io["hist"][:n]
+    assert np.all(np.abs(h - ho) <= 1e-9 * ho[0]), (h, ho)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "mixed_bf16"])
+def test_task_parallel_mixed_precision(precision):
+    pr = _problem("sipg3d_p2_8cube")
+    x_or, _ = OracleSolver.from_problem(pr, async_smooth=2).solve(pr.b, rtol=1e-10, maxiter=2000)
+    s = pkg.KCycleSolver(pr, precision=precision, use_graph=True, async_smooth=2)
+    x, info = s.solve(pr.b, rtol=1e-10, maxiter=2000)
+    s.close()
+    assert info["status"] == 0, info
+    _check_solution(pr, x, info, x_or)
+
+
+def test_task_parallel_graph_and_eager_are_bitwise_identical():
+    pr = make_problem(3, 2, (8, 8, 8), 3, seed=5)
+    out = []
+    for g in (False, True):
+        s = pkg.KCycleSolver(pr, precision="fp64", use_graph=g, async_smooth=3)
+        x, _ = s.solve(pr.b, rtol=1e-10)
+        s.close()
+        out.append(x)
+    assert np.array_equal(out[0], out[1])

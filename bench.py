@@ -210,7 +210,8 @@ def run_mrhs(pkg, rank, dev, stream, hbm_peak, args):
     pm = workload(wname).make(rank)
     B = torch.from_numpy(pm.b).to(dev)
     X = torch.zeros_like(B)
-    sm = pkg.KCycleSolver(pm, precision=prec_m, lmax=lmax_m, stream=stream.cuda_stream)
+    sm = pkg.KCycleSolver(pm, precision=prec_m, lmax=lmax_m, stream=stream.cuda_stream,
+                          async_smooth=HEADLINE_ASYNC_M)
     pkg.kcmg_solve(sm.ctx, B, X, RTOL, 0.0, 1)   # build the batched engine and autotune
     tune = sm.mrhs_tuning()
     X.zero_()
@@ -225,7 +226,8 @@ def run_mrhs(pkg, rank, dev, stream, hbm_peak, args):
     # mixed form) for comparison
     single = {}
     for prec in (() if args.no_single else ("fp64", prec_m)):
-        s1 = pkg.KCycleSolver(pm, precision=prec, use_graph=True, lmax=200, stream=stream.cuda_stream)
+        s1 = pkg.KCycleSolver(pm, precision=prec, use_graph=True, lmax=200, stream=stream.cuda_stream,
+                              async_smooth=HEADLINE_ASYNC_M)
         ts = []
         for j in (0, 1):
             bj = B[:, j].contiguous()
@@ -257,6 +259,7 @@ def run_mrhs(pkg, rank, dev, stream, hbm_peak, args):
         "ms_per_step": mms, "status": inf["status"], "rel_res": inf["rel_res"],
         "cycles": inf["iters"], "level_iters": inf["level_iters"][:pm.nlevels],
         "lmax": lmax_m, "precision": prec_m, "kernel_launches": inf["kernel_launches"],
+        "level0_cycle": f"Alg. AsyncMG, m = {HEADLINE_ASYNC_M} (every column)",
         "single_column_solves": single,
         "dtype": ("tensor-core TF32x3 smoother sweeps (FP32 accumulation)"
                   + (", BF16 block inverses" if prec_m == "mixed_bf16" else "")

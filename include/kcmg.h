@@ -99,7 +99,11 @@ typedef struct {
                                 stream while the smoother path applies m smoother + RM
                                 steps; one RM with the coarse correction closes the cycle.
                                 The level restarts when its basis could not take one more
-                                cycle (m + 1 vectors).  Single right-hand side only. */
+                                cycle (m + 1 vectors); level 0 holds lmax vectors plus one
+                                cycle's corrections.  Batched solves (nrhs > 1) run the same
+                                cycle per column, the coarse path first on one stream (it
+                                reads only the cycle-start residual, so the iterates are
+                                those of the concurrent form).  m in [0, 64]. */
 } kcmg_params;
 
 /* Fill p with the defaults of Sec. 4.2 / Alg. BJ for the given sizes (blocks, prolong

@@ -4,6 +4,7 @@
 // level's while loop is a conditional while node driven by device-side state.
 #include "kcmg_internal.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -734,6 +735,7 @@ MrhsView mrhs_view(kcmg_ctx* ctx) {
   v.lmax = ctx->p.lmax;
   v.precision = ctx->p.precision;
   v.tc_tf32_only = ctx->p.tc_tf32_only;
+  v.async_smooth = ctx->p.async_smooth;
   v.s = ctx->s;
   return v;
 }
@@ -871,7 +873,10 @@ kcmg_ctx* build_ctx(const kcmg_params* p, cudaStream_t user, const double* block
     // the per-level iteration caps (3 stored corrections per cycle)
     for (int l = 0; l < ctx->nlev - 1; ++l) {
       int cap;
-      if (l == 0) cap = p->lmax > 0 ? p->lmax + 3 : 512;
+      // level 0 holds lmax vectors plus one cycle's corrections (3 in Alg. 2, m + 1 in
+      // the task-parallel cycle): the restart test runs at the end of a cycle
+      const int per_cycle0 = std::max(3, p->async_smooth + 1);
+      if (l == 0) cap = (p->lmax > 0 ? p->lmax : 512 - per_cycle0) + per_cycle0;
       else cap = 3 * (p->lvl_maxit[l] > 0 ? p->lvl_maxit[l] : 1) + 3;
       if (p->lmax > 0 && l > 0 && p->lmax + 3 < cap) cap = p->lmax + 3;
       if (cap > kLcapMax) cap = kLcapMax;
@@ -881,6 +886,7 @@ kcmg_ctx* build_ctx(const kcmg_params* p, cudaStream_t user, const double* block
         CK(cudaMemGetInfo(&fr, &tot));
         const size_t per = (size_t)2 * ctx->lv[0].N * sizeof(double);
         while (cap > 16 && (size_t)cap * per > fr / 3) cap /= 2;
+        if (cap < per_cycle0 + 3) cap = per_cycle0 + 3;   // one cycle must always fit
       }
       alloc_cycle_vectors<double>(ctx, ctx->lv[l], cap);
       if (ctx->mixed) {   // FP32 smoother buffers

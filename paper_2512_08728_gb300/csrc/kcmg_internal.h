@@ -236,6 +236,7 @@ struct MrhsView {               // the context's hierarchy, as the batched solve
   int lmax;
   int precision;                         // kcmg_precision
   int tc_tf32_only;                      // single-product TF32 sweeps
+  int async_smooth;                      // level 0 as Alg. AsyncMG with this many smoother steps
   cudaStream_t s;
 };
 

@@ -45,7 +45,7 @@ struct MState {
   int nact, pad_f0, pad_f1, pad_f2;              // active columns after the last test
   int R, lcap, maxit, it;
   int iters_total, nrestart, status, guard;
-  int guard_cap, level, pad0, pad1;
+  int guard_cap, level, per_cycle, cap;    // restart when l + per_cycle > cap
   int act[kMaxRhs], l[kMaxRhs], flags[kMaxRhs], claim[kMaxRhs], brk[kMaxRhs], restart[kMaxRhs];
   double rtol, atol, brk_tol, pad2;
   double rnorm[kMaxRhs], rnorm0[kMaxRhs], eps[kMaxRhs], naz2[kMaxRhs], gam[kMaxRhs], alp[kMaxRhs];
@@ -700,7 +700,7 @@ __global__ void k_mctl(MState* st, const MState* parent, const double* __restric
         } else if (active && conv) {
           st->act[r] = 0;
         }
-        st->restart[r] = st->act[r] && !st->claim[r] && st->l[r] + 3 > lcap;
+        st->restart[r] = st->act[r] && !st->claim[r] && st->l[r] > 0 && st->l[r] + st->per_cycle > st->cap;
         f_restart = st->restart[r] != 0;
         f_any = st->act[r] != 0;
         break;
@@ -854,6 +854,7 @@ struct MLev {
   float* D32 = nullptr;          // natural FP32 inverses
   __nv_bfloat16* D16 = nullptr;  // natural BF16 inverses
   double *x = nullptr, *r = nullptr, *b = nullptr, *z = nullptr, *w = nullptr, *wre = nullptr, *t = nullptr;
+  double* zc = nullptr;          // level 0 of the task-parallel cycle: the coarse correction
   double *W = nullptr, *Z = nullptr;
   float *r32 = nullptr, *s0 = nullptr, *s1 = nullptr;
   int lcap = 0;
@@ -1040,11 +1041,12 @@ void smooth(MrhsEngine* E, int lev) {
   }
 }
 
-// Alg. 1 for every right-hand side at once on the correction L.z
-void rm(MrhsEngine* E, int lev) {
+// Alg. 1 for every right-hand side at once on the correction zcor (default: L.z)
+void rm(MrhsEngine* E, int lev, const double* zcor = nullptr) {
   MLev& L = E->lv[lev];
   const int R = E->R, g = gram_grid(L), thr = kGramWarps * 32;
-  spmm64(E, L, L.z, L.w, nullptr, 0);                                    // w = A z
+  const double* zz = zcor ? zcor : L.z;
+  spmm64(E, L, zz, L.w, nullptr, 0);                                     // w = A z
   k_mdots<<<g, thr, 0, E->s>>>(L.W, L.w, L.N, R, L.lcap, L.st, E->part, 0);
   reduce(E, g, L.lcap + 1, L.st, 1);
   ctl(E, lev, CTL_GRAM1);
@@ -1055,7 +1057,7 @@ void rm(MrhsEngine* E, int lev) {
   // otherwise the partials are stale but CTL_GRAM2 ignores them (no REORTH flags)
   reduce(E, g, L.lcap + 1, L.st, 1);
   ctl(E, lev, CTL_GRAM2);
-  k_mupdate<<<g, thr, 0, E->s>>>(L.W, L.Z, L.N, R, L.w, L.wre, L.z, L.r, L.st, E->cw, E->cz, E->part);
+  k_mupdate<<<g, thr, 0, E->s>>>(L.W, L.Z, L.N, R, L.w, L.wre, zz, L.r, L.st, E->cw, E->cz, E->part);
   E->launches++;
   reduce(E, g, 2, nullptr, 0);
   ctl(E, lev, CTL_UPDATE);
@@ -1076,11 +1078,12 @@ void restrict_to(MrhsEngine* E, int lev, bool start) {
   if (start) reduce(E, g, 1, nullptr, 0);
 }
 
-void prolong_from(MrhsEngine* E, int lev) {
+void prolong_from(MrhsEngine* E, int lev, double* target = nullptr) {
   MLev &F = E->lv[lev], &C = E->lv[lev + 1];
   const int g = grid_for(F.C, 8, 1 << 30);
+  double* zf = target ? target : F.z;
   MRHS_ND_SWITCH(E->v.np, E->v.dim, {
-    k_mprolong<NP, DIM><<<g, 256, 0, E->s>>>(C.x, F.n[0], F.n[1], F.C, C.n[0], C.n[1], E->v.P, E->R, F.z);
+    k_mprolong<NP, DIM><<<g, 256, 0, E->s>>>(C.x, F.n[0], F.n[1], F.C, C.n[0], C.n[1], E->v.P, E->R, zf);
   });
   E->launches++;
 }
@@ -1133,6 +1136,40 @@ void mg(MrhsEngine* E, int lev) {
   }
 }
 
+// Level 0 as Alg. AsyncMG with a fixed smoother count m (v.async_smooth): per cycle the
+// coarse path works on the cycle-start residual (restriction, MG on level 1 or the direct
+// solve, prolongation into zc); the smoother path applies m smoother + RM steps; one RM
+// with zc closes the cycle.  The batched engine runs on one stream, so the coarse path is
+// issued first: it reads only the cycle-start residual and writes only level >= 1 buffers
+// and zc, so the iterates are those of the concurrent form.
+void mg_async0(MrhsEngine* E) {
+  MLev& L = E->lv[0];
+  const int nlev = E->v.nlev;
+  for (;;) {
+    ctl(E, 0, CTL_TEST);
+    read_flags(E, 0);
+    E->hist_act.push_back(E->hst->nact);
+    if (E->hst->any_claim) { restart(E, 0, true); continue; }
+    if (!E->hst->any) break;
+    if (E->hst->any_restart) { restart(E, 0, false); continue; }
+    if (nlev == 2) {                                  // coarse path
+      restrict_to(E, 0, false);
+      coarse_solve(E);
+    } else {
+      restrict_to(E, 0, true);
+      ctl(E, 1, CTL_BEGIN, L.st);
+      mg(E, 1);
+    }
+    prolong_from(E, 0, L.zc);
+    for (int k = 0; k < E->v.async_smooth; ++k) {    // smoother path
+      smooth(E, 0);
+      rm(E, 0);
+    }
+    rm(E, 0, L.zc);                                   // the synchronisation
+    ctl(E, 0, CTL_ITEND);
+  }
+}
+
 // ---------------------------------------------------------------- setup of the engine
 void init_state(MrhsEngine* E, int lev, double rtol, double atol, int maxit, long long guard_cap) {
   MState h;
@@ -1145,6 +1182,9 @@ void init_state(MrhsEngine* E, int lev, double rtol, double atol, int maxit, lon
   h.atol = atol;
   h.brk_tol = 1e-14;
   h.guard_cap = (int)std::min<long long>(guard_cap, 1LL << 30);
+  h.per_cycle = (lev == 0 && E->v.async_smooth > 0) ? E->v.async_smooth + 1 : 3;
+  // the restart length: lmax where it binds (as in the single-column solve), else capacity
+  h.cap = (E->v.lmax > 0 && E->v.lmax < h.lcap) ? E->v.lmax : h.lcap;
   h.status = KCMG_OK;
   MCK(cudaMemcpyAsync(E->lv[lev].st, &h, sizeof h, cudaMemcpyHostToDevice, E->s));
 }
@@ -1276,11 +1316,13 @@ void build(MrhsEngine* E, const MrhsView& v, int R) {
     L.w = malloc_dev<double>(E, NR);
     L.wre = malloc_dev<double>(E, NR);
     L.t = malloc_dev<double>(E, NR);
+    if (l == 0 && v.async_smooth > 0) L.zc = malloc_dev<double>(E, NR);
     L.st = malloc_dev<MState>(E, 1);
     // basis capacity: level 0 from lmax (default 60), coarse levels from their iteration
     // caps (3 corrections per cycle); level 0 shrinks to what the device can hold
     int cap;
-    if (l == 0) cap = (v.lmax > 0 ? v.lmax : 60) + 3;
+    const int per_cycle0 = std::max(3, v.async_smooth + 1);   // corrections of one level-0 cycle
+    if (l == 0) cap = (v.lmax > 0 ? v.lmax : 60) + per_cycle0;
     else cap = 3 * std::max(1, v.lvl_maxit[l]) + 3;
     if (v.lmax > 0 && l > 0) cap = std::min(cap, v.lmax + 3);
     if (l == 0) {
@@ -1289,6 +1331,7 @@ void build(MrhsEngine* E, const MrhsView& v, int R) {
       const size_t per = 2 * NR * sizeof(double);
       const size_t budget = free_b > ((size_t)4 << 30) ? (size_t)((free_b - ((size_t)4 << 30)) * 0.8) : free_b / 2;
       while (cap > 6 && (size_t)cap * per > budget) cap = cap * 3 / 4;
+      if (cap < per_cycle0 + 3) cap = per_cycle0 + 3;   // one cycle must always fit
     }
     L.lcap = cap;
     L.W = malloc_dev<double>(E, (size_t)cap * NR);
@@ -1330,7 +1373,7 @@ void build(MrhsEngine* E, const MrhsView& v, int R) {
 
 kcmg_status mrhs_ensure(MrhsEngine** peng, const MrhsView& v, int R, std::string* err) {
   MrhsEngine* E = *peng;
-  if (E && (E->Ralloc != R || E->precision != v.precision)) {
+  if (E && (E->Ralloc != R || E->precision != v.precision || E->v.async_smooth != v.async_smooth)) {
     mrhs_destroy(E);
     E = *peng = nullptr;
   }
@@ -1404,7 +1447,8 @@ kcmg_status mrhs_solve(MrhsEngine** peng, const MrhsView& v, const double* b, do
     spmm64(E, L, L.x, L.r, L.b, 2);
     norms(E, L, L.r);
     ctl(E, 0, CTL_INIT0);
-    mg(E, 0);
+    if (v.async_smooth > 0) mg_async0(E);
+    else mg(E, 0);
     // final true residual
     spmm64(E, L, L.x, L.t, L.b, 2);
     norms(E, L, L.t);

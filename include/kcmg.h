@@ -112,7 +112,8 @@ void kcmg_default_params(kcmg_params *p, int dim, int np, const int n[3], int nl
 
 /* Convergence report.  hist/hist_type are caller-owned arrays of length hist_cap (may be
    NULL): ||r|| after every level-0 RM call with type 0 initial, 1 pre-smoother, 2 coarse
-   correction, 3 post-smoother, 4 restart (true residual replaces the recursive one);
+   correction, 3 post-smoother, 4 restart (true residual replaces the recursive one); the
+   task-parallel cycle records its m smoother RMs as type 1 and its coarse RM as type 2;
    batched solves record instead the active columns at each level-0 loop test (type 5). */
 typedef struct {
     int iters;                          /* level-0 cycles */
@@ -136,8 +137,8 @@ typedef struct {
    so that kcmg_last_error can explain the failure: destroy it in every case. */
 kcmg_status kcmg_setup(kcmg_ctx **out, const kcmg_params *p, void *cuda_stream);
 
-/* Solve A x = b (Alg. 2 at level 0) until ||b - A x|| <= max(rtol ||b - A x0||, atol)
-   or maxiter level-0 cycles.  x: in x0, out x.  info may be NULL.
+/* Solve A x = b (Alg. 2 at level 0, or Alg. AsyncMG when async_smooth > 0) until
+   ||b - A x|| <= max(rtol ||b - A x0||, atol) or maxiter level-0 cycles.  x: in x0, out x.  info may be NULL.
    nrhs in [1, 32].  With nrhs > 1, b and x are [N][nrhs] (right-hand sides fastest) and
    the columns are solved together: every column runs its own K-cycle (its own bases,
    Gram coefficients and level criteria, Alg. 2 / Alg. 1 per column) while all columns
@@ -145,8 +146,8 @@ kcmg_status kcmg_setup(kcmg_ctx **out, const kcmg_params *p, void *cuda_stream);
    it; a column that is not has its corrections discarded (masked).  Each column stops at
    ||b_j - A x_j|| <= max(rtol ||b_j - A x0_j||, atol), confirmed by a compensated FP64
    true residual.  The batched form is host-driven (use_graph is ignored).  Its level-0
-   basis holds lmax vectors per column (default 60 when lmax = 0), shrunk to what the
-   device can hold.  In the mixed forms the block-Jacobi sweeps run on the tensor cores
+   basis holds lmax vectors per column (default 60 when lmax = 0) plus one cycle's
+   corrections, shrunk to what the device can hold.  In the mixed forms the block-Jacobi sweeps run on the tensor cores
    (TF32 products, FP32 accumulation), with launch shapes chosen by an autotuner at the
    first batched solve (see kcmg_mrhs_tuning).  info: iters and level_iters count the
    shared loop; rel_res is the largest relative residual over the columns and res0 the

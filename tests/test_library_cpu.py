@@ -44,3 +44,23 @@ def test_status_strings():
     lib = pkg.load_library()
     assert lib.kcmg_status_string(0) == b"ok"
     assert lib.kcmg_status_string(4).startswith(b"singular")
+
+
+def test_default_params_follow_the_level_criteria():
+    """kcmg_default_params (host only): the level criteria of Sec. 4.2 and Alg. BJ's
+    omega and sweep count, the multiplicative cycle and three-product tensor-core sweeps."""
+    p = K.kcmg_default_params(3, 10, (64, 64, 64), 5)
+    assert (p.lvl_rtol[1], p.lvl_maxit[1]) == (0.1, 20)
+    assert (p.lvl_rtol[2], p.lvl_maxit[2]) == (0.5, 2)
+    assert all(p.lvl_maxit[l] == 1 for l in range(3, 5))
+    assert abs(p.omega - 0.7) < 1e-15 and p.sweeps == 5
+    assert p.async_smooth == 0 and p.tc_tf32_only == 0 and p.precision == K.KCMG_FP64
+
+
+def test_solve_rejects_mismatched_shapes_before_any_device_call():
+    import numpy as np
+    pkg.load_library()
+    with pytest.raises(ValueError):
+        K.kcmg_solve(None, np.zeros(8), np.zeros(9))
+    with pytest.raises(ValueError):
+        K.kcmg_solve(None, np.zeros((8, 2, 2)), np.zeros((8, 2, 2)))

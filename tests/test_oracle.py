@@ -388,3 +388,26 @@ def test_async_restart_keeps_basis_within_lmax():
     # between two restart entries (type 4) there are at most two cycles' corrections
     runs = np.split(t, np.where(t == 4)[0])
     assert max(int(np.sum(r != 4) - np.sum(r == 0)) for r in runs) <= 8
+
+
+@pytest.mark.parametrize("async_m", [0, 2])
+def test_exact_smoother_on_decoupled_cells_converges_after_one_correction(async_m):
+    """With no coupling between cells (all face blocks zero) the block-Jacobi inverse is
+    A^-1, so one sweep with omega = 1 from z = 0 gives z = A^-1 r and the first Alg. 1
+    call reaches the exact solution (the paper's special case of an exact smoother)."""
+    pr = make_problem(2, 2, (4, 4), 2, seed=2)
+    blocks = pr.blocks.copy()
+    blocks[1:] = 0.0                                   # decouple the cells
+    rng = np.random.default_rng(5)
+    for K in range(blocks.shape[1]):                  # well-conditioned SPD diagonal blocks
+        M = rng.standard_normal((pr.np_, pr.np_))
+        blocks[0, K] = M @ M.T + pr.np_ * np.eye(pr.np_)
+    S = OracleSolver(pr.d, pr.np_, pr.n, pr.nlevels, blocks, pr.prolong, omega=1.0, sweeps=1,
+                     async_smooth=async_m)
+    x, info = S.solve(pr.b, rtol=1e-12, maxiter=5)
+    h, t = info["hist"], info["hist_type"]
+    assert t[1] == 1                                  # the first correction is the smoother's
+    assert h[1] <= 1e-13 * h[0]
+    xs = np.concatenate([np.linalg.solve(blocks[0, K], pr.b[K * pr.np_:(K + 1) * pr.np_])
+                         for K in range(blocks.shape[1])])
+    assert np.linalg.norm(x - xs) <= 1e-12 * np.linalg.norm(xs)

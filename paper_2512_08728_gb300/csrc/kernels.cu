@@ -928,12 +928,12 @@ static Dims mkdims(const int* n) { Dims d; d.n[0] = n[0]; d.n[1] = n[1]; d.n[2] 
 // dispatch over the supported (np, dim) pairs; the body sees NP, DIM and S = 2 DIM + 1
 #define KCMG_ND_SWITCH(np, dim, ...)                                                      \
   switch (np * 10 + dim) {                                                                \
-    case 32: { constexpr int NP = 3, DIM = 2, S = 5; (void)S; __VA_ARGS__; } break;       \
-    case 62: { constexpr int NP = 6, DIM = 2, S = 5; (void)S; __VA_ARGS__; } break;       \
-    case 102: { constexpr int NP = 10, DIM = 2, S = 5; (void)S; __VA_ARGS__; } break;     \
-    case 43: { constexpr int NP = 4, DIM = 3, S = 7; (void)S; __VA_ARGS__; } break;       \
-    case 103: { constexpr int NP = 10, DIM = 3, S = 7; (void)S; __VA_ARGS__; } break;     \
-    case 203: { constexpr int NP = 20, DIM = 3, S = 7; (void)S; __VA_ARGS__; } break;     \
+    case 32: { constexpr int NP = 3, DIM = 2, S = 5; (void)S; (void)DIM; __VA_ARGS__; } break;       \
+    case 62: { constexpr int NP = 6, DIM = 2, S = 5; (void)S; (void)DIM; __VA_ARGS__; } break;       \
+    case 102: { constexpr int NP = 10, DIM = 2, S = 5; (void)S; (void)DIM; __VA_ARGS__; } break;     \
+    case 43: { constexpr int NP = 4, DIM = 3, S = 7; (void)S; (void)DIM; __VA_ARGS__; } break;       \
+    case 103: { constexpr int NP = 10, DIM = 3, S = 7; (void)S; (void)DIM; __VA_ARGS__; } break;     \
+    case 203: { constexpr int NP = 20, DIM = 3, S = 7; (void)S; (void)DIM; __VA_ARGS__; } break;     \
     default: break;                                                                       \
   }
 #define KCMG_NP_SWITCH(np, ...)                               \

@@ -159,7 +159,8 @@ def oracle_sample(pr, level1_total, cycles_total, async_m=None):
     c1 = t_visit / k1
     c0 = max(t_cycle - l1 * c1, 0.0)
     t_full = cycles_total * c0 + level1_total * c1
-    txt = (f"first level-0 cycle of the solve (Alg. AsyncMG, m = {am}; {l1} level-1 iterations) "
+    cyc = f"Alg. AsyncMG, m = {am}" if am > 0 else "Alg. 2"
+    txt = (f"first level-0 cycle of the solve ({cyc}; {l1} level-1 iterations) "
            f"in {t_cycle:.2f} s and one level-1 visit on its own ({k1} iterations) in "
            f"{t_visit:.2f} s (setup {t_setup:.1f} s, not counted): {c0:.2f} s of level-0 work "
            f"per cycle, {c1:.3f} s per level-1 iteration, extrapolated to the {cycles_total} "
@@ -284,6 +285,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--async-m", type=int, default=None,
+                    help="level-0 cycle of the headline solve: smoother steps of Alg. AsyncMG "
+                         "(default %d); 0 = the multiplicative cycle of Alg. 2" % HEADLINE_ASYNC_M)
     ap.add_argument("--mrhs-only", action="store_true",
                     help="run only the batched form (profiling runs): skips the single-RHS solves")
     ap.add_argument("--mrhs-workload", default=None,
@@ -331,8 +335,9 @@ def main():
             print(json.dumps({"mrhs": out}), flush=True)
         return
     pr = workload(args.workload).make(rank)
+    head_m = HEADLINE_ASYNC_M if args.async_m is None else args.async_m
     s = pkg.KCycleSolver(pr, precision="fp64", use_graph=not args.eager, lmax=LMAX,
-                         async_smooth=HEADLINE_ASYNC_M,
+                         async_smooth=head_m,
                          stream=stream.cuda_stream)
     b = torch.from_numpy(pr.b).to(dev)
     x = torch.zeros_like(b)
@@ -461,7 +466,7 @@ def main():
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        v, t, txt = oracle_sample(pr, int(lvl[1]), int(cycles))
+        v, t, txt = oracle_sample(pr, int(lvl[1]), int(cycles), async_m=head_m)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": txt}
 
     if rank == 0:
@@ -473,8 +478,9 @@ def main():
             "config": {"workload": args.workload, "cells": list(pr.n), "p": pr.p, "dofs": pr.ndof,
                        "levels": pr.nlevels, "nu_ratio": 1000, "smoother": "block-Jacobi omega 0.7, 5 sweeps",
                        "rtol": RTOL, "lmax": LMAX, "cuda_graph": not args.eager, "coarse_cycle": "persistent",
-                       "level0_cycle": f"Alg. AsyncMG: coarse path on a second stream, {HEADLINE_ASYNC_M} "
-                                       "smoother + RM steps per cycle beside it (task-parallel OrthoMG)",
+                       "level0_cycle": (f"Alg. AsyncMG: coarse path on a second stream, {head_m} "
+                                        "smoother + RM steps per cycle beside it (task-parallel OrthoMG)")
+                                       if head_m > 0 else "Alg. 2 (multiplicative K-cycle)",
                        "parallelism": "replicas" if ws > 1 else "single GPU",
                        "l2": "inputs larger than L2 (operator 1.47 GB vs 129 MB L2): no flush"},
             "status": status, "rel_res": rel, "cycles": cycles, "level_iters": lvl[:pr.nlevels],

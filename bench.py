@@ -16,11 +16,18 @@ operator (1.47 GB) is larger than the 129 MB L2, so no flush is needed between s
 Under torchrun every rank solves its own replica (seed = rank): the method has no
 data-parallel split on one node here ("replicas only"), so there is no collective.
 
---impl reference times the CPU oracle (oracle/, plain single-threaded C) on the same
-workload: each step is a bounded sample (the first level-0 cycle), extrapolated to the full
-solve by the level-1 iteration count of the GPU solve.
+Timed work: the headline solve at --steps solves after --warmup; each extra form (the
+multiplicative cycle, the mixed forms) one solve after its capture; the end-to-end leg
+through host buffers at most three solves.  Setup (hierarchy, inverses, graph capture) is
+timed separately and reported as setup_s.
+
+--impl reference times the CPU oracle (oracle/, plain C; its OpenMP build on all host
+cores) on the same workload: each step is a bounded sample (the first level-0 cycle and
+one level-1 visit), extrapolated to the full solve by the level-0 cycle and level-1
+iteration counts of the GPU solve.
 """
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -59,10 +66,40 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-# FP64 FMA throughput of this GPU measured with a dependent-chain microbenchmark
-# (profiles/fp64_alu_peak_gb300.md): 1.198 TFLOP/s, i.e. 4.79 TB/s of operator data at
-# one FP64 FMA per 8-byte element.
-FP64_TFLOPS = 1.198
+# FP64 FMA peak of GB300 from its unit counts and clock: 152 SMs x 2 FP64 FMA per clock
+# per SM x 2 flop x 2.07 GHz = 1.259 TFLOP/s (NVIDIA's nominal 1.25 TFLOP/s).  Kernels
+# that do one FP64 FMA per 8-byte element they read are bound by it at 5.03 TB/s, below
+# the measured HBM copy bandwidth.
+GB300_SMS = 152
+FP64_FMA_PER_CLK_PER_SM = 2
+SM_MAX_GHZ = 2.07
+FP64_TFLOPS = GB300_SMS * FP64_FMA_PER_CLK_PER_SM * 2 * SM_MAX_GHZ / 1e3
+FP64_PEAK_NOTE = ("FP64 FMA peak from unit counts and clock: 152 SMs x 2 FMA/clk x 2 flop x "
+                  "2.07 GHz = %.3f TFLOP/s, i.e. %.0f GB/s of 8-byte operands at one FMA each"
+                  % (FP64_TFLOPS, FP64_TFLOPS * 1e3 / 2 * 8))
+
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernels
+# the bench reports, from one ncu capture each, keyed by kernel; valid only while the
+# kernel's sources hash to the recorded value (otherwise the line reports null).
+TRAFFIC = {}
+
+
+def _sources_sha(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2512_08728_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel):
+    t = TRAFFIC.get(kernel)
+    if not t:
+        return None, None
+    per_launch, sha, files, note = t
+    if _sources_sha(files) != sha:
+        return None, "kernel changed since the capture (" + note + ")"
+    return per_launch, note
 
 
 class ClockSampler:
@@ -123,7 +160,7 @@ def _dist():
     return ws, rank, local
 
 
-def oracle_sample(pr, level1_total, cycles_total, async_m=None):
+def oracle_sample(pr, level1_total, cycles_total, async_m=None, openmp=False):
     """Time the CPU oracle on a bounded sample of the headline solve and extrapolate.
 
     The sample is the first level-0 cycle (the same cycle as the headline) plus one level-1
@@ -134,13 +171,14 @@ def oracle_sample(pr, level1_total, cycles_total, async_m=None):
     cycles_total x (level-0 cost) + level1_total x (level-1 cost).  The level-0 cost of
     the first cycle is a lower bound for later cycles (their Gram work grows with the
     basis), so the estimate errs towards a faster oracle.
-    Returns (dof_per_s, seconds_of_the_sample, text)."""
-    import numpy as np
-
+    openmp: the OpenMP build of the oracle on all host cores (its parallel loops give
+    bitwise the serial results).
+    Returns (dof_per_s, seconds_of_the_sample, text, cores)."""
     import oracle
     am = HEADLINE_ASYNC_M if async_m is None else async_m
+    cores = oracle.threads(0) if openmp else 1
     t0 = time.perf_counter()
-    orc = oracle.OracleSolver.from_problem(pr, lmax=LMAX, async_smooth=am)
+    orc = oracle.OracleSolver.from_problem(pr, lmax=LMAX, async_smooth=am, openmp=openmp)
     t_setup = time.perf_counter() - t0
     t0 = time.perf_counter()
     x, info = orc.solve(pr.b, rtol=RTOL, maxiter=1)
@@ -150,7 +188,7 @@ def oracle_sample(pr, level1_total, cycles_total, async_m=None):
     rt, mi = oracle.default_level_criteria(pr.nlevels)
     n1 = [v // 2 for v in pr.n]
     o1 = oracle.OracleSolver(pr.d, pr.np_, n1, pr.nlevels - 1, orc.blocks(1), pr.prolong,
-                             lvl_rtol=rt[1:], lvl_maxit=mi[1:])
+                             lvl_rtol=rt[1:], lvl_maxit=mi[1:], openmp=openmp)
     b1 = orc.restrict(0, pr.b)
     t0 = time.perf_counter()
     _, i1 = o1.solve(b1, rtol=float(rt[1]), maxiter=int(mi[1]))
@@ -160,13 +198,14 @@ def oracle_sample(pr, level1_total, cycles_total, async_m=None):
     c0 = max(t_cycle - l1 * c1, 0.0)
     t_full = cycles_total * c0 + level1_total * c1
     cyc = f"Alg. AsyncMG, m = {am}" if am > 0 else "Alg. 2"
-    txt = (f"first level-0 cycle of the solve ({cyc}; {l1} level-1 iterations) "
+    txt = (f"{cores} host thread{'s' if cores > 1 else ''}: "
+           f"first level-0 cycle of the solve ({cyc}; {l1} level-1 iterations) "
            f"in {t_cycle:.2f} s and one level-1 visit on its own ({k1} iterations) in "
            f"{t_visit:.2f} s (setup {t_setup:.1f} s, not counted): {c0:.2f} s of level-0 work "
            f"per cycle, {c1:.3f} s per level-1 iteration, extrapolated to the {cycles_total} "
            f"cycles and {level1_total} level-1 iterations of the full solve: {t_full:.0f} s")
     del orc, o1, x
-    return pr.ndof / t_full, t_cycle + t_visit, txt
+    return pr.ndof / t_full, t_cycle + t_visit, txt, cores
 
 
 def run_reference(args, ws, rank):
@@ -176,8 +215,9 @@ def run_reference(args, ws, rank):
     pr = workload(WORKLOAD).make(0)
     vals = []
     txt = ""
+    cores = 1
     for k in range(args.warmup + args.steps):
-        v, t, txt = oracle_sample(pr, GPU_LEVEL1_ITERS_FP64, GPU_CYCLES_FP64)
+        v, t, txt, cores = oracle_sample(pr, GPU_LEVEL1_ITERS_FP64, GPU_CYCLES_FP64, openmp=True)
         if k >= args.warmup:
             vals.append((v, t))
     value = statistics.median(v for v, _ in vals)
@@ -187,8 +227,8 @@ def run_reference(args, ws, rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded SIPG workload)",
             "config": {"workload": WORKLOAD, "dofs": pr.ndof, "rtol": RTOL, "lmax": LMAX},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": txt},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "host_cores": os.cpu_count(), "sample": txt},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -285,6 +325,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--all-forms", action="store_true",
+                    help="also time the mixed forms with the multiplicative cycle (about 30 s each)")
     ap.add_argument("--async-m", type=int, default=None,
                     help="level-0 cycle of the headline solve: smoother steps of Alg. AsyncMG "
                          "(default %d); 0 = the multiplicative cycle of Alg. 2" % HEADLINE_ASYNC_M)
@@ -336,16 +378,24 @@ def main():
         return
     pr = workload(args.workload).make(rank)
     head_m = HEADLINE_ASYNC_M if args.async_m is None else args.async_m
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter()
     s = pkg.KCycleSolver(pr, precision="fp64", use_graph=not args.eager, lmax=LMAX,
-                         async_smooth=head_m,
-                         stream=stream.cuda_stream)
+                         async_smooth=head_m, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_setup
     b = torch.from_numpy(pr.b).to(dev)
     x = torch.zeros_like(b)
 
-    def solve(sv, bb, xx):
+    def solve(sv, bb, xx, maxiter=None):
         xx.zero_()
-        return pkg.kcmg_solve(sv.ctx, bb, xx, RTOL, 0.0, args.maxiter)
+        return pkg.kcmg_solve(sv.ctx, bb, xx, RTOL, 0.0, args.maxiter if maxiter is None else maxiter)
 
+    # the first solve captures the CUDA graph; it is timed as part of the setup
+    t0 = time.perf_counter()
+    solve(s, b, x, maxiter=1)
+    torch.cuda.synchronize()
+    capture_s = time.perf_counter() - t0
     for _ in range(args.warmup):
         info = solve(s, b, x)
     s.kernel_report()   # reset the coarse-cycle counters
@@ -376,45 +426,52 @@ def main():
     launches = sum(i["kernel_launches"] for i in infos)
     rep = s.kernel_report(reps=10)
 
-    # roofline of the dominant kernel: the persistent coarse cycle (device timer + exact
-    # algorithmic bytes per launch, accumulated over the timed region)
+    # The persistent coarse cycle times itself (GPU global timer at entry and after its
+    # last barrier, accumulated over every launch of the timed region) and counts the
+    # algorithmic bytes of every phase it runs.  Its data stays in the 129 MB L2 and its
+    # arithmetic is FP64 (one FMA per 8-byte operand), so its roofline is the FP64 FMA
+    # rate expressed as operand bytes per second; the HBM fraction is given beside it.
+    # The level-0 operator and sweep kernels are timed standalone with CUDA events on the
+    # library's stream (kernels inside a CUDA graph cannot be bracketed by events).
+    fp64_gbs = FP64_TFLOPS * 1e3 / 2 * 8
     cl = max(1, rep["coarse_launches"])
     coarse_ms = rep["coarse_ms"] / cl
     coarse_bytes = rep["coarse_bytes"] / cl
     coarse_gbs = coarse_bytes / (coarse_ms * 1e-3) / 1e9 if coarse_ms > 0 else 0.0
     share = rep["coarse_ms"] / ms if ms > 0 else 0.0
-    fp64_gbs = FP64_TFLOPS * 1e12 / 2 * 8 / 1e9   # operator bytes/s at the FP64 FMA peak
-    # The coarse cycle's data (operators of 41K and 5K rows, their bases) stays in the
-    # 129 MB L2: ncu measures ~1% of its algorithmic bytes as DRAM traffic, so HBM does not
-    # bound it.  Its arithmetic is FP64 (one FMA per 8-byte operator element), and the
-    # binding roofline is the FP64 FMA rate, expressed as operator bytes per second.
+    spmv_gbs = rep["spmv_bytes"] / (rep["spmv_ms"] * 1e-3) / 1e9
+    sweep_gbs = rep["sweep_bytes"] / (rep["sweep_ms"] * 1e-3) / 1e9
     kernels = [
-        {"name": "k_coarse_cycle (levels 2-4 at 64^3, persistent)", "bound": "alu",
+        {"name": "k_coarse_cycle", "what": "persistent coarse cycle (levels below the first "
+         "level with <= 100,000 rows)", "bound": "alu",
          "achieved": coarse_gbs, "peak": fp64_gbs, "unit": "GB/s",
          "frac": coarse_gbs / fp64_gbs, "hbm_frac": coarse_gbs / hbm_peak,
-         "ms_per_launch": coarse_ms,
+         "ms_per_launch": coarse_ms, "launches_per_step": rep["coarse_launches"] / args.steps,
          "bytes_per_launch": coarse_bytes, "share_of_step": share,
          "ms_per_launch_by_level": [v / cl for v in rep["coarse_level_ms"][:pr.nlevels]],
          "ms_per_launch_by_phase": {k: v / cl for k, v in rep["coarse_phase_ms"].items()}},
-        {"name": "k_spmv level 0 FP64 (Alg. 1 operator)", "bound": "alu",
-         "achieved": rep["spmv_bytes"] / (rep["spmv_ms"] * 1e-3) / 1e9,
-         "peak": fp64_gbs, "unit": "GB/s",
-         "frac": rep["spmv_bytes"] / (rep["spmv_ms"] * 1e-3) / 1e9 / fp64_gbs,
+        {"name": "k_spmv", "what": "level-0 FP64 operator application (Alg. 1: w = A z)",
+         "bound": "alu", "achieved": spmv_gbs, "peak": fp64_gbs, "unit": "GB/s",
+         "frac": spmv_gbs / fp64_gbs, "hbm_frac": spmv_gbs / hbm_peak,
          "ms_per_launch": rep["spmv_ms"], "bytes_per_launch": rep["spmv_bytes"]},
-        {"name": "k_bj_sweep level 0 FP64", "bound": "alu",
-         "achieved": rep["sweep_bytes"] / (rep["sweep_ms"] * 1e-3) / 1e9,
-         "peak": fp64_gbs, "unit": "GB/s",
-         "frac": rep["sweep_bytes"] / (rep["sweep_ms"] * 1e-3) / 1e9 / fp64_gbs,
+        {"name": "k_bj_sweep", "what": "level-0 FP64 block-Jacobi sweep (Alg. BJ)", "bound": "alu",
+         "achieved": sweep_gbs, "peak": fp64_gbs, "unit": "GB/s",
+         "frac": sweep_gbs / fp64_gbs, "hbm_frac": sweep_gbs / hbm_peak,
          "ms_per_launch": rep["sweep_ms"], "bytes_per_launch": rep["sweep_bytes"]},
     ]
+    dom = kernels[0]
+    traffic, traffic_note = _traffic(dom["name"])
 
-    # end to end through the C interface with host buffers (copies inside the timing)
+    # end to end through the C interface with pinned host buffers: every step copies b
+    # and x0 to the device and x back inside the timed region
     e2e = None
     if not args.no_e2e:
-        bh = np.ascontiguousarray(pr.b)
-        xh = np.zeros(pr.ndof)
+        k_e2e = max(1, min(args.steps, 3))
+        bh = torch.from_numpy(pr.b).pin_memory().numpy()
+        xh = torch.zeros(pr.ndof, dtype=torch.float64).pin_memory().numpy()
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(k_e2e):
             xh[:] = 0.0
             pkg.kcmg_solve(s.ctx, bh, xh, RTOL, 0.0, args.maxiter)
         t_e2e = time.perf_counter() - t0
@@ -422,31 +479,37 @@ def main():
             t = torch.tensor([t_e2e], device=dev)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             t_e2e = float(t.item())
-        e2e = {"value": ws * pr.ndof * args.steps / t_e2e, "unit": UNIT,
-               "h2d_bytes_per_step": 2 * pr.ndof * 8, "d2h_bytes_per_step": pr.ndof * 8}
+        e2e = {"value": ws * pr.ndof * k_e2e / t_e2e, "unit": UNIT, "steps": k_e2e,
+               "h2d_bytes_per_step": 2 * pr.ndof * 8, "d2h_bytes_per_step": pr.ndof * 8,
+               "host_buffers": "pinned"}
     s.close()
 
+    # the other forms: one timed solve each, after the solve that captures its graph
     forms = {}
     if not args.no_mixed:
-        for prec, am in (("fp64", 0), ("mixed", HEADLINE_ASYNC_M), ("mixed_bf16", HEADLINE_ASYNC_M),
-                         ("mixed", 0), ("mixed_bf16", 0)):
+        plan = [("fp64", 0), ("mixed", HEADLINE_ASYNC_M), ("mixed_bf16", HEADLINE_ASYNC_M)]
+        if args.all_forms:
+            plan += [("mixed", 0), ("mixed_bf16", 0)]
+        for prec, am in plan:
+            if prec == "fp64" and am == head_m:
+                continue
             sm = pkg.KCycleSolver(pr, precision=prec, use_graph=True, lmax=LMAX,
                                   stream=stream.cuda_stream, async_smooth=am)
-            pkg.kcmg_solve(sm.ctx, b, x, RTOL, 0.0, 2)   # capture the graph
+            solve(sm, b, x, maxiter=1)   # capture the graph
             sm.kernel_report()
             torch.cuda.synchronize()
             e0.record(stream)
-            inf = [solve(sm, b, x) for _ in range(args.steps)]
+            inf = solve(sm, b, x)
             e1.record(stream)
             torch.cuda.synchronize()
             mms = e0.elapsed_time(e1)
             rp = sm.kernel_report(reps=10)
-            sw_peak = hbm_peak if prec != "fp64" else FP64_TFLOPS * 1e12 / 2 * 8 / 1e9
+            sw_peak = hbm_peak if prec != "fp64" else fp64_gbs
             fname = (f"{prec}_multiplicative" if am == 0 else f"{prec}_task_parallel_m{am}")
             forms[fname] = {
-                "value": pr.ndof * args.steps / (mms * 1e-3), "unit": UNIT,
-                "ms_per_step": mms / args.steps, "status": [i["status"] for i in inf],
-                "rel_res": max(i["rel_res"] for i in inf), "cycles": inf[-1]["iters"],
+                "value": pr.ndof / (mms * 1e-3), "unit": UNIT, "timed_solves": 1,
+                "ms_per_step": mms, "status": inf["status"],
+                "rel_res": inf["rel_res"], "cycles": inf["iters"],
                 "dtype": ("f32 smoother sweeps" + (", bf16 block inverses" if prec == "mixed_bf16" else "")
                           + "; f64 residual minimisation, transfers, coarsest solve") if prec != "fp64" else "f64",
                 "cycle": ("Alg. 2 (multiplicative K-cycle)" if am == 0 else
@@ -466,8 +529,17 @@ def main():
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        v, t, txt = oracle_sample(pr, int(lvl[1]), int(cycles), async_m=head_m)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": txt}
+        v1, t1, txt1, _ = oracle_sample(pr, int(lvl[1]), int(cycles), async_m=head_m)
+        cpu = {"value": v1, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "host_cores": os.cpu_count(), "sample": txt1}
+        try:
+            vn, tn, txtn, cores = oracle_sample(pr, int(lvl[1]), int(cycles), async_m=head_m,
+                                                openmp=True)
+            cpu = {"value": vn, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "host_cores": os.cpu_count(), "sample": txtn,
+                   "single_core": {"value": v1, "unit": UNIT, "cores": 1, "sample": txt1}}
+        except Exception as e:   # noqa: BLE001  (no OpenMP build on this host)
+            cpu["all_core"] = f"unavailable: {e}"
 
     if rank == 0:
         line = {
@@ -483,13 +555,13 @@ def main():
                                        if head_m > 0 else "Alg. 2 (multiplicative K-cycle)",
                        "parallelism": "replicas" if ws > 1 else "single GPU",
                        "l2": "inputs larger than L2 (operator 1.47 GB vs 129 MB L2): no flush"},
+            "setup_s": setup_s, "graph_capture_s": capture_s,
             "status": status, "rel_res": rel, "cycles": cycles, "level_iters": lvl[:pr.nlevels],
-            "roofline": {"bound": kernels[0]["bound"], "achieved": kernels[0]["achieved"],
-                         "peak": kernels[0]["peak"], "unit": "GB/s", "frac": kernels[0]["frac"],
-                         "traffic": None,
-                         "peak_kind": "measured FP64 FMA rate (1.198 TFLOP/s, profiles/fp64_alu_peak_gb300.md) "
-                                      "as operator bytes/s; HBM peak " + f"{hbm_peak} GB/s ({peak_kind})",
-                         "kernel": kernels[0]["name"]},
+            "roofline": {"bound": dom["bound"], "achieved": dom["achieved"],
+                         "peak": dom["peak"], "unit": dom["unit"], "frac": dom["frac"],
+                         "traffic": traffic, "traffic_note": traffic_note,
+                         "peak_kind": FP64_PEAK_NOTE + f"; HBM peak {hbm_peak} GB/s ({peak_kind})",
+                         "kernel": dom["name"]},
             "kernels": kernels,
             "forms": forms,
             "e2e": e2e,

@@ -207,21 +207,23 @@ kcmg_status kcmg_rm_sequence(kcmg_ctx *ctx, int level, const double *b, const do
 kcmg_status kcmg_kernel_report(kcmg_ctx *ctx, int reps, double *out, int nout);
 
 /* r = b - A x with the finest-level FP64 operator, and *rnorm = ||r|| (a host double),
-   for callers that must not allocate device memory: for example host code inside a
-   stream capture, real-time loops that may not block on the driver's allocator, or
-   processes whose device memory pool a framework owns.  The paper has no counterpart;
-   this is a service of the library.
+   for callers that must not allocate device memory: processes whose device memory is
+   already claimed (for example by a framework's caching allocator that holds most of the
+   free memory, where a cudaMalloc fails or forces the framework to release its cache),
+   code running under a fixed device-memory budget, and error-recovery paths after an
+   out-of-memory failure.  The paper has no counterpart; this is a service of the library.
    b, x, r: device pointers of length N (anything else returns KCMG_INVALID_ARG).
    The call allocates nothing: its reduction scratch is a static device array of 257 KB,
    present on every GPU that loads the library until the process exits.  It handles up to
    32768 thread blocks (up to 10,485,760 rows at np = 10 or 20, 9,437,184 at np = 3 or 6,
-   8,388,608 at np = 4); larger problems return KCMG_INVALID_ARG.  The first call on a
-   device looks up the scratch's address there (cudaGetSymbolAddress, with that device
-   current); make that first call before any stream capture.  All calls share the scratch
-   and it keeps the last call's contents (the reduction counter is cleared at every call):
-   calls that overlap on the GPU (other streams, other host threads, other contexts on the
-   same device) race and must not be issued.  Stream-ordered on the context's stream;
-   returns after *rnorm is written. */
+   8,388,608 at np = 4); larger problems return KCMG_INVALID_ARG.  kcmg_setup looks up the
+   scratch's device address (cudaGetSymbolAddress, with the context's device current) and
+   loads the call's kernels, so the call does no set-up of its own; the call runs on the
+   context's device (it makes that device current for its duration).  All calls share the
+   scratch and it keeps the last call's contents (the reduction counter is cleared at every
+   call): calls that overlap on the GPU (other streams, other host threads, other contexts
+   on the same device) race and must not be issued.  Stream-ordered on the context's
+   stream; it copies ||r|| to host memory and synchronises that stream before returning. */
 kcmg_status kcmg_residual_noalloc(kcmg_ctx *ctx, const double *b, const double *x, double *r,
                                   double *rnorm);
 

@@ -12,10 +12,10 @@ monotone residuals, manufactured solutions, P^T P = I and polynomial reproductio
 transfers, the Galerkin energy identity, and central finite differences of the adjoint
 gradient.
 """
-from .oracle import (OracleSolver, build, grad_lognu, default_level_criteria,
+from .oracle import (OracleSolver, build, grad_lognu, default_level_criteria, threads,
                      ORC_OK, ORC_NOT_CONVERGED, ORC_BREAKDOWN, ORC_NONFINITE, ORC_SINGULAR,
                      ORC_INVALID_ARG)
 
-__all__ = ["OracleSolver", "build", "grad_lognu", "default_level_criteria", "ORC_OK",
+__all__ = ["OracleSolver", "build", "grad_lognu", "default_level_criteria", "threads", "ORC_OK",
            "ORC_NOT_CONVERGED", "ORC_BREAKDOWN", "ORC_NONFINITE", "ORC_SINGULAR",
            "ORC_INVALID_ARG"]

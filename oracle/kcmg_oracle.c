@@ -45,6 +45,20 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Loops over cells or over vector elements whose every output element is computed by the
+   same sequential arithmetic whichever thread runs it.  Built with -fopenmp they run on
+   all host cores and give bitwise the results of the serial build; every sum over
+   elements (dot products, the restriction's accumulation into a coarse cell) stays
+   sequential. */
+#ifdef _OPENMP
+#define ORC_PARALLEL_FOR _Pragma("omp parallel for schedule(static)")
+#else
+#define ORC_PARALLEL_FOR
+#endif
 
 #define ORC_MAXLEV 16
 
@@ -96,6 +110,7 @@ static int ndof(const osolver *S, int lev) { return S->lv[lev].ncell * S->np; }
 static void apply(const osolver *S, int lev, const double *x, double *y) {
     const olevel *L = &S->lv[lev];
     int np = S->np, nf = 2 * S->dim;
+    ORC_PARALLEL_FOR
     for (int K = 0; K < L->ncell; K++) {
         for (int i = 0; i < np; i++) {
             double s = 0.0;
@@ -118,7 +133,9 @@ static void smooth(osolver *S, int lev, const double *b, double *x) {
     for (int i = 0; i < N; i++) x[i] = 0.0;
     for (int k = 0; k < S->sweeps; k++) {
         apply(S, lev, x, r);
+        ORC_PARALLEL_FOR
         for (int i = 0; i < N; i++) r[i] = b[i] - r[i];
+        ORC_PARALLEL_FOR
         for (int K = 0; K < L->ncell; K++) {
             const double *D = L->inv + (size_t)K * np * np;
             for (int i = 0; i < np; i++) {
@@ -165,6 +182,7 @@ static void restrict_(const osolver *S, int lev, const double *rf, double *rc) {
 /* z = P z_c : child k of coarse cell J gets P_k z_c[J] */
 static void prolong(const osolver *S, int lev, const double *zc, double *zf) {
     int np = S->np;
+    ORC_PARALLEL_FOR
     for (int K = 0; K < S->lv[lev].ncell; K++) {
         int k, J = parent_of(S, lev, K, &k);
         const double *Pk = S->P + (size_t)k * np * np;
@@ -336,7 +354,9 @@ static int rm_step(osolver *S, int lev, double *z) {
         for (int i = 0; i < L->l; i++) {                   /* for all columns w_i of W */
             const double *Wi = L->W + (size_t)i * N, *Zi = L->Z + (size_t)i * N;
             double beta = dot(N, Wi, w);                   /* beta := w_i . w_{l+1} */
+            ORC_PARALLEL_FOR
             for (int k = 0; k < N; k++) w[k] -= beta * Wi[k];
+            ORC_PARALLEL_FOR
             for (int k = 0; k < N; k++) z[k] -= beta * Zi[k];
         }
         if (sqrt(dot(N, w, w)) >= 0.5 * before) break;    /* second pass only if needed */
@@ -347,9 +367,11 @@ static int rm_step(osolver *S, int lev, double *z) {
     double gamma = 1.0 / nw;                               /* gamma := 1/||w_{l+1}|| */
     ensure_cap(S, L);
     double *Wl = L->W + (size_t)L->l * N, *Zl = L->Z + (size_t)L->l * N;
+    ORC_PARALLEL_FOR
     for (int k = 0; k < N; k++) { Wl[k] = gamma * w[k]; Zl[k] = gamma * z[k]; }
     L->alpha[L->l] = dot(N, Wl, L->r0);                    /* alpha_{l+1} := w_{l+1} . r0 */
     L->l++;
+    ORC_PARALLEL_FOR
     for (int k = 0; k < N; k++) {                          /* x := x0 + Z alpha; r := r0 - W alpha */
         double xs = L->x0[k], rs = L->r0[k];
         for (int i = 0; i < L->l; i++) {
@@ -685,3 +707,15 @@ int orc_basis_size(void *h, int lev) { return ((osolver *)h)->lv[lev].l; }
 int orc_restarts(void *h) { return ((osolver *)h)->restarts; }
 /* m > 0: level 0 runs Alg. AsyncMG with m smoother steps per cycle; 0: Alg. 2 */
 void orc_set_async(void *h, int m) { ((osolver *)h)->async_m = m > 0 ? m : 0; }
+/* threads of the OpenMP build's parallel loops (n <= 0: all host cores); returns the
+   number in use, 1 for the serial build */
+int orc_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    else omp_set_num_threads(omp_get_num_procs());
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}

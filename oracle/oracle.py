@@ -13,28 +13,37 @@ ORC_OK, ORC_NOT_CONVERGED, ORC_BREAKDOWN, ORC_NONFINITE, ORC_SINGULAR, ORC_INVAL
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "kcmg_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "_build", "liboracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 _dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 _ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle into oracle/_build/liboracle.so (plain -O2, single thread)."""
-    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle into oracle/_build/liboracle.so (plain -O2, single thread) or,
+    with openmp=True, the same source with -fopenmp into liboracle_omp.so: its cell- and
+    element-parallel loops then run on all host cores with bitwise the serial results."""
+    lib = _LIB_OMP if openmp else _LIB
+    os.makedirs(os.path.dirname(lib), exist_ok=True)
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+        tmp = lib + f".{os.getpid()}.tmp"
+        flags = ["-fopenmp"] if openmp else []
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", *flags, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, lib)
+    return lib
 
 
-def _load():
-    global _lib
+def threads(n: int = 0) -> int:
+    """Threads of the OpenMP build (n <= 0: all host cores); returns the count in use."""
+    return int(_load(True).orc_threads(int(n)))
+
+
+def _load(openmp: bool = False):
     with _lock:
-        if _lib is None:
-            lib = C.CDLL(build())
+        if openmp not in _libs:
+            lib = C.CDLL(build(openmp=openmp))
             lib.orc_create.restype = C.c_void_p
             lib.orc_create.argtypes = [C.c_int, C.c_int, _ip, C.c_int, _dp, _dp, C.c_double,
                                        C.c_int, _dp, _ip, C.c_int, C.c_int, C.POINTER(C.c_int)]
@@ -60,8 +69,10 @@ def _load():
             lib.orc_basis_size.restype = C.c_int
             lib.orc_basis_size.argtypes = [C.c_void_p, C.c_int]
             lib.orc_grad_lognu.argtypes = [C.c_int, C.c_int, _ip, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
-            _lib = lib
-    return _lib
+            lib.orc_threads.restype = C.c_int
+            lib.orc_threads.argtypes = [C.c_int]
+            _libs[openmp] = lib
+    return _libs[openmp]
 
 
 def default_level_criteria(nlevels: int):
@@ -84,8 +95,9 @@ class OracleSolver:
     """FP64 CPU K-cycle OrthoMG on a Cartesian block-ELL operator and its hierarchy."""
 
     def __init__(self, dim, np_, n, nlevels, blocks, prolong, omega=0.7, sweeps=5,
-                 lvl_rtol=None, lvl_maxit=None, lmax=0, transpose=False, async_smooth=0):
-        self._lib = _load()
+                 lvl_rtol=None, lvl_maxit=None, lmax=0, transpose=False, async_smooth=0,
+                 openmp=False):
+        self._lib = _load(openmp)
         rt, mi = default_level_criteria(nlevels)
         if lvl_rtol is not None:
             rt = np.asarray(lvl_rtol, dtype=np.float64)

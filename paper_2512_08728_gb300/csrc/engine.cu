@@ -44,6 +44,8 @@ struct Level {
 struct kcmg_ctx {
   kcmg_params p{};
   int dim = 0, np = 0, S = 0, nlev = 0, nch = 0;
+  int dev = 0;                        // the device the context was built on
+  double* na_scratch = nullptr;       // static scratch of kcmg_residual_noalloc on dev
   bool mixed = false;
   cudaStream_t user = nullptr, s = nullptr;
   cudaStream_t cap[KCMG_MAX_LEVELS + 2] = {};
@@ -845,6 +847,7 @@ kcmg_ctx* build_ctx(const kcmg_params* p, cudaStream_t user, const double* block
     ctx->user = user;
     int dev = 0;
     CK(cudaGetDevice(&dev));
+    ctx->dev = dev;
     CK(cudaStreamCreateWithFlags(&ctx->s, cudaStreamNonBlocking));
     for (int l = 0; l < KCMG_MAX_LEVELS + 1; ++l) CK(cudaStreamCreateWithFlags(&ctx->cap[l], cudaStreamNonBlocking));
     {  // the coarse path of the task-parallel cycle (eager form): highest priority, so
@@ -997,6 +1000,8 @@ kcmg_ctx* build_ctx(const kcmg_params* p, cudaStream_t user, const double* block
     for (auto& L : ctx->lv) maxN = maxN > (size_t)L.N ? maxN : (size_t)L.N;
     ctx->stage_in = dalloc<double>(ctx, maxN);
     ctx->stage_out = dalloc<double>(ctx, maxN);
+    // the no-allocation residual's static scratch on this device (address and kernels)
+    CK(noalloc_prepare(dev, &ctx->na_scratch));
     CK(cudaStreamSynchronize(ctx->s));
     *out_status = KCMG_OK;
     return ctx;
@@ -1368,9 +1373,16 @@ kcmg_status kcmg_residual_noalloc(kcmg_ctx* ctx, const double* b, const double* 
       REQUIRE(dev, "kcmg_residual_noalloc: b, x and r must be device memory");
     }
     const Level& L = ctx->lv[0];
-    Level0View v{L.A64, L.nbr, L.N, L.G, L.rows_pad, L.block_rows, ctx->np, ctx->dim, ctx->s};
+    Level0View v{L.A64, L.nbr, L.N, L.G, L.rows_pad, L.block_rows, ctx->np, ctx->dim, ctx->s,
+                 ctx->na_scratch};
+    // run on the context's device (its scratch address, operator and stream live there)
+    int cur = 0;
+    CK(cudaGetDevice(&cur));
+    if (cur != ctx->dev) CK(cudaSetDevice(ctx->dev));
     int too_large = 0;
-    CK(residual_noalloc(v, b, x, r, rnorm, &too_large));
+    const cudaError_t e = residual_noalloc(v, b, x, r, rnorm, &too_large);
+    if (cur != ctx->dev) CK(cudaSetDevice(cur));
+    CK(e);
     REQUIRE(!too_large, "kcmg_residual_noalloc: %d rows need more than the 32768 thread blocks "
             "its static scratch holds", L.N);
     return KCMG_OK;

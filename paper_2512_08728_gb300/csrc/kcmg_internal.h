@@ -210,7 +210,11 @@ struct Level0View {
   const int* nbr;
   int N, G, rows_pad, block_rows, np, dim;
   cudaStream_t stream;
+  double* scratch;   // device address of the static scratch (from noalloc_prepare)
 };
+// With device dev current: look up the static scratch's device address (once per device)
+// and load the no-allocation kernels.  Called by kcmg_setup.
+cudaError_t noalloc_prepare(int dev, double** scratch);
 cudaError_t residual_noalloc(const Level0View& v, const double* b, const double* x, double* r,
                              double* rnorm_host, int* too_large);
 

@@ -1,16 +1,20 @@
 // kcmg_residual_noalloc: the residual r = b - A x of the finest-level FP64 operator and its
 // norm, for callers that must not allocate device memory.
 //
-// Which callers cannot allocate: code that runs where cudaMalloc is forbidden or unsafe.
-// Examples are host code inside a stream capture (an allocation there would break or
-// serialise the capture), real-time or embedded loops that may not block on the driver's
-// allocator, and hosts whose memory pool is fixed by a framework.  They still build a
-// context once with kcmg_setup; this call then needs nothing beyond the caller's buffers.
+// Which callers cannot allocate: processes whose device memory is already claimed, for
+// example by a framework's caching allocator that holds most of the free memory (a
+// cudaMalloc there fails or forces the framework to release its cache), code that runs
+// under a fixed device-memory budget, and error-recovery paths that run after an
+// out-of-memory failure.  They still build a context once with kcmg_setup (which
+// allocates); this call then needs nothing beyond the caller's buffers.
 //
 // The regular residual kernel keeps its per-block partial sums and its reduction counter
 // in buffers the context allocates.  This variant keeps them in one file-scope static
 // device array instead, so the call itself allocates nothing (no cudaMalloc, no cudaFree,
-// no allocating library routine).
+// no allocating library routine).  kcmg_setup looks up the array's device address (with
+// the context's device current) and loads this file's kernels, so that a later call does
+// no set-up of its own.  The call reads ||r|| into host memory and synchronises the
+// context's stream before it returns.
 #include "kcmg_internal.h"
 
 #include <mutex>
@@ -42,8 +46,10 @@ __device__ __forceinline__ double na_block_sum(double v, double* sh) {
   return r;
 }
 
-// r = b - A x with ||r||^2 reduced through the static scratch (same row mapping and
-// accumulation order as the context's residual kernel, so r is bitwise the same).
+// r = b - A x with ||r||^2 reduced through the static scratch.  One thread per DOF row,
+// plain FP64 fused multiply-adds over the row's slots: r equals the plain FP64 operator
+// application b - A x of the library's operator kernel to rounding (the solver's own
+// level-0 residual is compensated, double-double, and may differ in the last bits).
 template <int NP, int S>
 __global__ void __launch_bounds__(320)
 k_residual_noalloc(const double* __restrict__ A, const int* __restrict__ nbr, int N, int G,
@@ -98,31 +104,40 @@ k_residual_noalloc(const double* __restrict__ A, const int* __restrict__ nbr, in
 std::mutex g_na_mutex;
 void* g_na_ptr[256] = {};
 
-cudaError_t noalloc_scratch(int dev, double** out) {
+}  // namespace
+
+cudaError_t noalloc_prepare(int dev, double** scratch) {
   std::lock_guard<std::mutex> lock(g_na_mutex);
   if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+  int cur = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return e;
+  if (cur != dev) return cudaErrorInvalidDevice;   // the caller makes dev current
   if (!g_na_ptr[dev]) {
     void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);   // device is current
-    if (e != cudaSuccess) return e;
+    // the host-side name of the array is not a device address: ask the runtime for it
+    if ((e = cudaGetSymbolAddress(&p, g_noalloc_scratch)) != cudaSuccess) return e;
+    // load the kernels now (lazy module loading would otherwise do it at the first call)
+    cudaFuncAttributes fa;
+    const void* fns[] = {(const void*)k_residual_noalloc<3, 5>, (const void*)k_residual_noalloc<6, 5>,
+                         (const void*)k_residual_noalloc<10, 5>, (const void*)k_residual_noalloc<4, 7>,
+                         (const void*)k_residual_noalloc<10, 7>, (const void*)k_residual_noalloc<20, 7>};
+    for (const void* f : fns)
+      if ((e = cudaFuncGetAttributes(&fa, f)) != cudaSuccess) return e;
     g_na_ptr[dev] = p;
   }
-  *out = static_cast<double*>(g_na_ptr[dev]);
+  *scratch = static_cast<double*>(g_na_ptr[dev]);
   return cudaSuccess;
 }
-
-}  // namespace
 
 cudaError_t residual_noalloc(const Level0View& v, const double* b, const double* x, double* r,
                              double* rnorm_host, int* too_large) {
   const int grid = v.rows_pad / v.block_rows;
   *too_large = grid > kNoallocMaxBlocks;
   if (*too_large) return cudaSuccess;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  double* scratch = nullptr;
-  if ((e = noalloc_scratch(dev, &scratch)) != cudaSuccess) return e;
+  double* scratch = v.scratch;
+  if (!scratch) return cudaErrorInvalidValue;
+  cudaError_t e;
   // the counter must start at zero (the previous call may have been interrupted)
   if ((e = cudaMemsetAsync(scratch + kNoallocMaxBlocks + 1, 0, sizeof(double), v.stream)) != cudaSuccess) return e;
   switch (v.np * 10 + v.dim) {

@@ -325,3 +325,55 @@ def test_task_parallel_graph_and_eager_are_bitwise_identical():
         s.close()
         out.append(x)
     assert np.array_equal(out[0], out[1])
+
+
+# ------------------------------------------------------------------ the benchmark's level layout
+def _layout_solve(pr, m, rows_max, monkeypatch, lmax=200, rtol=1e-10):
+    """Solve with the persistent coarse kernel taking the levels from the first one with at
+    most rows_max rows (set through KCMG_PERSISTENT_ROWS at setup); the levels above it run
+    one kernel per step under nested conditional graph nodes."""
+    monkeypatch.setenv("KCMG_PERSISTENT_ROWS", str(rows_max))
+    s = pkg.KCycleSolver(pr, precision="fp64", use_graph=True, coarse_persistent=True,
+                         async_smooth=m, lmax=lmax)
+    monkeypatch.delenv("KCMG_PERSISTENT_ROWS")
+    x, info = s.solve(pr.b, rtol=rtol, maxiter=2000)
+    rep = s.kernel_report()
+    s.close()
+    return x, info, rep
+
+
+@pytest.mark.parametrize("m", [0, 8])
+def test_benchmark_level_layout_matches_oracle(m, monkeypatch):
+    """The 64^3 benchmark runs level 1 as full-occupancy kernels under a nested conditional
+    node and levels 2-3 in the persistent kernel, inside the task-parallel (m = 8, Alg.
+    AsyncMG) or multiplicative (m = 0, Alg. 2) level-0 cycle.  The same layout on 16^3
+    cells, p = 2, 5 levels (l1 5,120 rows nested; l2 640 and l3 80 rows persistent; l4
+    direct), against the oracle's solve of the same cycle."""
+    pr = make_problem(3, 2, (16, 16, 16), 5, seed=3)
+    x, info, rep = _layout_solve(pr, m, 1000, monkeypatch)
+    assert info["status"] == 0, info
+    lv = rep["coarse_level_ms"]
+    assert lv[1] == 0.0 and lv[2] > 0.0 and lv[3] > 0.0     # the layout really ran
+    x_or, io = OracleSolver.from_problem(pr, async_smooth=m, lmax=200, openmp=True).solve(
+        pr.b, rtol=1e-10, maxiter=2000)
+    assert io["status"] == 0
+    _check_solution(pr, x, info, x_or)
+
+
+def test_benchmark_level_layout_32cube_task_parallel_matches_oracle(monkeypatch):
+    """32^3 cells, p = 2 (327,680 DOFs), 5 levels, Alg. AsyncMG with m = 8 and lmax = 200 as
+    the benchmark: level 1 (40,960 rows) nested, levels 2-3 persistent, level 4 direct.
+
+    Both sides solve to 3e-11.  At this size (condition number near 1e7) two iterates that
+    both meet a relative residual of 1e-10 can differ by more than 1e-8: measured 1.3e-8.
+    The difference is bounded by the sum of their errors, each at most ||A^-1|| times its
+    residual, so a tighter stop on both sides keeps it inside the 1e-8 bound."""
+    pr = make_problem(3, 2, (32, 32, 32), 5, seed=0)
+    x, info, rep = _layout_solve(pr, 8, 10000, monkeypatch, rtol=3e-11)
+    assert info["status"] == 0, info
+    lv = rep["coarse_level_ms"]
+    assert lv[1] == 0.0 and lv[2] > 0.0
+    x_or, io = OracleSolver.from_problem(pr, async_smooth=8, lmax=200, openmp=True).solve(
+        pr.b, rtol=3e-11, maxiter=2000)
+    assert io["status"] == 0
+    _check_solution(pr, x, info, x_or)

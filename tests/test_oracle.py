@@ -411,3 +411,23 @@ def test_exact_smoother_on_decoupled_cells_converges_after_one_correction(async_
     xs = np.concatenate([np.linalg.solve(blocks[0, K], pr.b[K * pr.np_:(K + 1) * pr.np_])
                          for K in range(blocks.shape[1])])
     assert np.linalg.norm(x - xs) <= 1e-12 * np.linalg.norm(xs)
+
+
+# ------------------------------------------------------------------ all-core build
+@pytest.mark.parametrize("m", [0, 4])
+def test_openmp_build_gives_bitwise_the_serial_results(m):
+    """The OpenMP build of the oracle (the benchmark's all-core CPU baseline) runs only its
+    cell- and element-parallel loops on several threads; every sum stays sequential, so
+    solves, histories and level counts are bitwise those of the serial build."""
+    import oracle
+    assert oracle.threads(4) >= 1
+    pr = make_problem(3, 2, (8, 8, 8), 3, seed=4)
+    out = []
+    for omp in (False, True):
+        x, info = _solver(pr, openmp=omp, async_smooth=m).solve(pr.b, rtol=1e-10, maxiter=200)
+        assert info["status"] == ORC_OK
+        out.append((x, info))
+    (x0, i0), (x1, i1) = out
+    assert np.array_equal(x0, x1)
+    assert np.array_equal(i0["hist"], i1["hist"]) and i0["iters"] == i1["iters"]
+    assert np.array_equal(i0["level_iters"], i1["level_iters"])

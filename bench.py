@@ -487,7 +487,8 @@ def main():
     # the other forms: one timed solve each, after the solve that captures its graph
     forms = {}
     if not args.no_mixed:
-        plan = [("fp64", 0), ("mixed", HEADLINE_ASYNC_M), ("mixed_bf16", HEADLINE_ASYNC_M)]
+        plan = [("fp64", 0), ("mixed", HEADLINE_ASYNC_M), ("mixed_bf16", HEADLINE_ASYNC_M),
+                ("ir32", HEADLINE_ASYNC_M), ("ir32_bf16", HEADLINE_ASYNC_M)]
         if args.all_forms:
             plan += [("mixed", 0), ("mixed_bf16", 0)]
         for prec, am in plan:
@@ -506,12 +507,23 @@ def main():
             rp = sm.kernel_report(reps=10)
             sw_peak = hbm_peak if prec != "fp64" else fp64_gbs
             fname = (f"{prec}_multiplicative" if am == 0 else f"{prec}_task_parallel_m{am}")
+            ir = prec.startswith("ir32")
+            if ir:
+                dtype = ("f64 iterative refinement (compensated f64 residual) around an f32 inner "
+                         "K-cycle: f32 operators, sweeps, transfers, bases"
+                         + (", bf16 block inverses" if prec == "ir32_bf16" else "")
+                         + "; f64 Gram reductions and coarsest solve")
+            elif prec != "fp64":
+                dtype = ("f32 smoother sweeps" + (", bf16 block inverses" if prec == "mixed_bf16" else "")
+                         + "; f64 residual minimisation, transfers, coarsest solve")
+            else:
+                dtype = "f64"
             forms[fname] = {
                 "value": pr.ndof / (mms * 1e-3), "unit": UNIT, "timed_solves": 1,
                 "ms_per_step": mms, "status": inf["status"],
                 "rel_res": inf["rel_res"], "cycles": inf["iters"],
-                "dtype": ("f32 smoother sweeps" + (", bf16 block inverses" if prec == "mixed_bf16" else "")
-                          + "; f64 residual minimisation, transfers, coarsest solve") if prec != "fp64" else "f64",
+                "refinements": inf["refinements"] if ir else None,
+                "dtype": dtype,
                 "cycle": ("Alg. 2 (multiplicative K-cycle)" if am == 0 else
                           f"Alg. AsyncMG on level 0: coarse path on a second stream, {am} smoother "
                           f"+ RM steps per cycle beside it"),

@@ -57,7 +57,17 @@ typedef enum {
                               in FP64.  The FP64 minimisation over FP32-computed corrections
                               is the iterative refinement: the attainable residual is
                               FP64's */
-    KCMG_MIXED_BF16INV = 2 /* as KCMG_MIXED with the block-Jacobi inverses stored in BF16 */
+    KCMG_MIXED_BF16INV = 2,/* as KCMG_MIXED with the block-Jacobi inverses stored in BF16 */
+    KCMG_IR32 = 3,         /* FP64 iterative refinement around an FP32 inner solve.  Outer
+                              loop in FP64: r = b - A x with the FP64 operator (compensated
+                              sums), stop when ||r|| <= max(rtol ||r0||, atol); otherwise solve
+                              A e = r / ||r|| by the K-cycle entirely in FP32 (FP32 operators
+                              for w = A z and the sweeps, FP32 transfers, vectors and bases
+                              W, Z) with FP64 reductions for the Gram coefficients and norms
+                              and the FP64 dense coarsest solve, to ||r_in|| <= ir_inner_rtol;
+                              then x += ||r|| e in FP64.  A refinement step that does not
+                              lower the FP64 residual is rolled back and ends the solve. */
+    KCMG_IR32_BF16INV = 4  /* as KCMG_IR32 with the block-Jacobi inverses stored in BF16 */
 } kcmg_precision;
 
 /* Setup input: the fine operator, the hierarchy and the smoother/cycle parameters. */
@@ -104,6 +114,11 @@ typedef struct {
                                 cycle per column, the coarse path first on one stream (it
                                 reads only the cycle-start residual, so the iterates are
                                 those of the concurrent form).  m in [0, 64]. */
+    double ir_inner_rtol;    /* KCMG_IR32*: relative tolerance of every inner FP32 solve
+                                (default 1e-3; in (0, 1)) */
+    int ir_max_steps;        /* KCMG_IR32*: cap on FP64 refinement steps (default 64) */
+    int ir_inner_maxit;      /* KCMG_IR32*: cap on level-0 cycles of one inner solve (default
+                                300; the solve's maxiter caps their sum) */
 } kcmg_params;
 
 /* Fill p with the defaults of Sec. 4.2 / Alg. BJ for the given sizes (blocks, prolong

@@ -111,12 +111,13 @@ struct LvScal {
   double rnorm, rnorm0, eps;
 };
 
-// Vectors, basis W, Z, the Alg. 1 operator and the transfers are FP64 (T = double); the
-// smoother sweeps run in TS with inverses stored as TI.
-template <typename TS, typename TI, int NP, int DIM>
+// Vectors, basis W, Z, the Alg. 1 operator and the transfers are in TV (FP64, or FP32 in
+// the inner solve of the iterative-refinement forms); the smoother sweeps run in TS with
+// inverses stored as TI.  Reductions and Gram coefficients are FP64 in every form.
+template <typename TV, typename TS, typename TI, int NP, int DIM>
 struct CoarseCycle {
-  using T = double;
-  using V2 = double2;
+  using T = TV;
+  using V2 = typename V2T<TV>::type;
   using VS2 = typename V2T<TS>::type;
   static constexpr int S = 2 * DIM + 1;
   static constexpr int NF = S - 1;
@@ -214,7 +215,7 @@ struct CoarseCycle {
   __device__ double spmv(int lev, const T* x, T* y, const T* b) {
     const CoarseLevel& C = L(lev);
     const T* A = static_cast<const T*>(C.A);
-    count(opbytes(C, S, 8) + (double)C.N * 8 * (b ? 3 : 2));
+    count(opbytes(C, S, sizeof(T)) + (double)C.N * sizeof(T) * (b ? 3 : 2));
     double nrm = 0.0;
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < C.rows_pad; row += gridDim.x * blockDim.x) {
       if (row >= C.N) continue;
@@ -248,7 +249,7 @@ struct CoarseCycle {
   template <typename TO>
   __device__ void sweep(const CoarseLevel& C, const T* r, const TS* zo, TO* zn, bool first) {
     count(opbytes(C, first ? 0 : S - 1, a.smoother_bytes) + opbytes(C, 1, a.inverse_bytes) +
-          (double)C.N * (8 + sizeof(TO) + (first ? 0 : sizeof(TS))));
+          (double)C.N * (sizeof(T) + sizeof(TO) + (first ? 0 : sizeof(TS))));
     const TS* A = static_cast<const TS*>(C.As);
     const TI* D = static_cast<const TI*>(C.Dinv);
     const TS om = (TS)a.omega;
@@ -332,7 +333,7 @@ struct CoarseCycle {
     double* part = a.partial + (size_t)(rcount & 1) * a.partial_stride;
     rcount++;
     dots(W, N, w, l, part);
-    count((double)(l + 1) * N * 8);
+    count((double)(l + 1) * N * sizeof(T));
     if (!reduce_cols(part, nc)) return false;
     ph(PH_RM_GRAM1);
     double hh = 0.0;
@@ -355,7 +356,7 @@ struct CoarseCycle {
       double* part2 = a.partial + (size_t)(rcount & 1) * a.partial_stride;
       rcount++;
       dots(W, N, wre, l, part2);
-      count((double)(l + 2) * N * 8 + (double)(l + 1) * N * 8);   // apply + second dots
+      count((double)(l + 2) * N * sizeof(T) + (double)(l + 1) * N * sizeof(T));   // apply + second dots
       if (!reduce_cols(part2, nc)) return false;
       for (int i = threadIdx.x; i < l; i += blockDim.x) {
         cw[kCoarseMaxCols + i] += red_s[i];   // z gets h + h2
@@ -389,7 +390,7 @@ struct CoarseCycle {
       nw2 = fma((double)av, (double)av, nw2);
       wr = fma((double)av, (double)ldv(r + j), wr);
     }
-    count((double)(2 * l + 5) * N * 8);   // W, Z columns; w, z, r in; new columns out
+    count((double)(2 * l + 5) * N * sizeof(T));   // W, Z columns; w, z, r in; new columns out
     {
       double v[2] = {nw2, wr};
       if (!reduce_few<2>(v)) return false;
@@ -416,7 +417,7 @@ struct CoarseCycle {
       }
       r2 = fma((double)rv, (double)rv, r2);
     }
-    count(discard ? 0.0 : (double)N * 8 * 8);
+    count(discard ? 0.0 : (double)N * 8 * sizeof(T));
     // ||r - alpha w||^2 = ||r||^2 - alpha^2 for unit w with alpha = w . r; reduce the
     // updated vector explicitly only if that cancels more than four digits
     const double r2old = sc.rnorm * sc.rnorm;
@@ -463,7 +464,7 @@ struct CoarseCycle {
   // b_{lev+1} = R r_lev; with start: r_{lev+1} = b_{lev+1}, x_{lev+1} = 0; returns ||b||^2 part
   __device__ double restrict_(int lev, bool start) {
     const CoarseLevel &F = L(lev), &C = L(lev + 1);
-    count((double)F.N * 8 + (double)C.N * 8 * (start ? 3 : 1));
+    count((double)F.N * sizeof(T) + (double)C.N * sizeof(T) * (start ? 3 : 1));
     const T* rf = vec(F.r);
     T* bc = vec(C.b);
     double nrm = 0.0;
@@ -491,7 +492,7 @@ struct CoarseCycle {
   // z_lev = P x_{lev+1}
   __device__ void prolong(int lev) {
     const CoarseLevel &F = L(lev), &C = L(lev + 1);
-    count((double)F.N * 8 + (double)C.N * 8);
+    count((double)F.N * sizeof(T) + (double)C.N * sizeof(T));
     const T* xc = vec(C.x);
     T* zf = vec(F.z);
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < F.N; row += gridDim.x * blockDim.x) {
@@ -509,7 +510,7 @@ struct CoarseCycle {
   // x_c = A_c^{-1} b_c (FP64 dense inverse), one warp per row
   __device__ void coarse_solve(int lev) {
     const CoarseLevel& C = L(lev);
-    count((double)a.Nc * a.Nc * 8 + (double)a.Nc * 16);
+    count((double)a.Nc * a.Nc * 8 + (double)a.Nc * 2 * sizeof(T));
     const T* bc = vec(C.b);
     T* xc = vec(C.x);
     const int warps = (gridDim.x * blockDim.x) >> 5;
@@ -638,9 +639,9 @@ struct CoarseCycle {
   }
 };
 
-template <typename TS, typename TI, int NP, int DIM>
+template <typename TV, typename TS, typename TI, int NP, int DIM>
 __global__ void __launch_bounds__(320, 1) k_coarse_cycle(CoarseArgs a) {
-  using T = double;
+  using T = TV;
   extern __shared__ unsigned char smem_raw[];
   __shared__ double sh[32 * 8];
   __shared__ double red_s[kCoarseMaxCols];
@@ -648,10 +649,10 @@ __global__ void __launch_bounds__(320, 1) k_coarse_cycle(CoarseArgs a) {
   constexpr int NCH = 1 << DIM;
   T* Ps = reinterpret_cast<T*>(smem_raw);   // prolongation matrices first (8-byte aligned)
   TS* tile = reinterpret_cast<TS*>(Ps + NCH * NP * NP);
-  const T* P = static_cast<const T*>(a.P);
-  for (int i = threadIdx.x; i < NCH * NP * NP; i += blockDim.x) Ps[i] = P[i];
+  const double* P = static_cast<const double*>(a.P);   // FP64 prolongation matrices
+  for (int i = threadIdx.x; i < NCH * NP * NP; i += blockDim.x) Ps[i] = (T)P[i];
   __syncthreads();
-  CoarseCycle<TS, TI, NP, DIM> cc{a, sh, red_s, tile, Ps, cw};
+  CoarseCycle<TV, TS, TI, NP, DIM> cc{a, sh, red_s, tile, Ps, cw};
   unsigned long long t0 = 0;
   if (blockIdx.x == 0 && threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
   // start of MG on the first coarse level: b, r, x were set by the restriction kernel
@@ -663,7 +664,7 @@ __global__ void __launch_bounds__(320, 1) k_coarse_cycle(CoarseArgs a) {
   }
   double v[1] = {nb};
   if (!cc.reduce_few<1>(v)) return;
-  cc.count((double)C.N * 8);
+  cc.count((double)C.N * sizeof(T));
   cc.run(a.lev0);   // reads ||b||^2 from red_s[0]
   // device time of this launch: every block has passed the last barrier of the cycle
   if (cc.ok) cc.ok = cc.bar();

@@ -45,6 +45,8 @@ struct kcmg_ctx {
   kcmg_params p{};
   int dim = 0, np = 0, S = 0, nlev = 0, nch = 0;
   int dev = 0;                        // the device the context was built on
+  bool ir = false;                    // FP64 iterative refinement around an FP32 inner solve
+  double *xo = nullptr, *bo = nullptr, *xt = nullptr;   // its FP64 outer x, b and trial x
   double* na_scratch = nullptr;       // static scratch of kcmg_residual_noalloc on dev
   bool mixed = false;
   cudaStream_t user = nullptr, s = nullptr;
@@ -139,6 +141,15 @@ void copy_out(kcmg_ctx* ctx, double* dst, const double* src, size_t n) {
 
 int level_cells(const int* n, int dim) { return n[0] * n[1] * (dim == 3 ? n[2] : 1); }
 
+// operator of a level's residual minimisation and the prolongation matrices, in the
+// level's vector type (FP64; FP32 in the inner solve of the iterative-refinement forms)
+template <typename V> const V* level_op(const Level& L);
+template <> const double* level_op<double>(const Level& L) { return L.A64; }
+template <> const float* level_op<float>(const Level& L) { return L.A32; }
+template <typename V> const V* prolong_mats(const kcmg_ctx* c);
+template <> const double* prolong_mats<double>(const kcmg_ctx* c) { return c->P64; }
+template <> const float* prolong_mats<float>(const kcmg_ctx* c) { return c->P32; }
+
 // ------------------------------------------------------------------ setup
 void setup_level_geometry(kcmg_ctx* ctx, Level& L, int l) {
   for (int j = 0; j < 3; ++j) L.n[j] = (j < ctx->dim) ? (ctx->p.n[j] >> l) : 1;
@@ -219,7 +230,7 @@ void build_hierarchy(kcmg_ctx* ctx, const double* blocks_src) {
     if (ctx->mixed) {
       L.A32 = dalloc<float>(ctx, opsz);
       launch_interleave<float>(np, S, L.nat, L.ncell, L.G, L.A32, ctx->s);
-      if (ctx->p.precision == KCMG_MIXED_BF16INV) {
+      if (ctx->p.precision == KCMG_MIXED_BF16INV || ctx->p.precision == KCMG_IR32_BF16INV) {
         L.D16 = dalloc<__nv_bfloat16>(ctx, invsz);
         launch_interleave<__nv_bfloat16>(np, 1, inv_nat, L.ncell, L.G, L.D16, ctx->s);
       } else {
@@ -260,10 +271,12 @@ void launch_coarse(kcmg_ctx* ctx, cudaStream_t s) {
   CK(cudaMemsetAsync(ctx->cc.bar_count, 0, sizeof(unsigned int), s));   // barrier counter
   cudaError_t err;
   const int thr = ctx->lv[ctx->cc_lev0].block_rows;
-  if (!ctx->mixed) err = launch_coarse_cycle<double, double>(ctx->cc, ctx->cc_grid, thr, s);
-  else if (ctx->p.precision == KCMG_MIXED_BF16INV)
-    err = launch_coarse_cycle<float, __nv_bfloat16>(ctx->cc, ctx->cc_grid, thr, s);
-  else err = launch_coarse_cycle<float, float>(ctx->cc, ctx->cc_grid, thr, s);
+  const bool bf16 = ctx->p.precision == KCMG_MIXED_BF16INV || ctx->p.precision == KCMG_IR32_BF16INV;
+  if (!ctx->mixed) err = launch_coarse_cycle<double, double, double>(ctx->cc, ctx->cc_grid, thr, s);
+  else if (ctx->ir && bf16) err = launch_coarse_cycle<float, float, __nv_bfloat16>(ctx->cc, ctx->cc_grid, thr, s);
+  else if (ctx->ir) err = launch_coarse_cycle<float, float, float>(ctx->cc, ctx->cc_grid, thr, s);
+  else if (bf16) err = launch_coarse_cycle<double, float, __nv_bfloat16>(ctx->cc, ctx->cc_grid, thr, s);
+  else err = launch_coarse_cycle<double, float, float>(ctx->cc, ctx->cc_grid, thr, s);
   CK(err);
 }
 
@@ -371,11 +384,11 @@ struct Cycle {
     launches += 3;                                                         // transfers, restart check
     if (lev + 1 == ctx->nlev - 1) {                                        // direct solve
       launches += 1;
-      launch_restrict<V, V>(ctx->np, ctx->dim, L.n, C.n, ctx->P64, static_cast<V*>(L.r),
+      launch_restrict<V, V>(ctx->np, ctx->dim, L.n, C.n, prolong_mats<V>(ctx), static_cast<V*>(L.r),
                             static_cast<V*>(C.b), nullptr, nullptr, nullptr, EpiArgs{}, s);
       launch_coarse_gemv<V>(ctx->Ainv, ctx->Nc, static_cast<V*>(C.b), static_cast<V*>(C.x), s);
     } else if (ctx->coarse_kernel && lev + 1 == ctx->cc_lev0) {            // small levels in
-      launch_restrict<V, V>(ctx->np, ctx->dim, L.n, C.n, ctx->P64, static_cast<V*>(L.r),  // one
+      launch_restrict<V, V>(ctx->np, ctx->dim, L.n, C.n, prolong_mats<V>(ctx), static_cast<V*>(L.r),  // one
                             static_cast<V*>(C.b), static_cast<V*>(C.r), static_cast<V*>(C.x),  // launch
                             nullptr, EpiArgs{}, s);
       launches += 1;
@@ -391,19 +404,19 @@ struct Cycle {
         CK(cudaStreamGetCaptureInfo(s, &cs, &id, &g, &deps, &ed, &nd));
         CK(cudaGraphConditionalHandleCreate(&handle[lev + 1], g, 0, 0));
       }
-      launch_restrict<V, V>(ctx->np, ctx->dim, L.n, C.n, ctx->P64, static_cast<V*>(L.r),
+      launch_restrict<V, V>(ctx->np, ctx->dim, L.n, C.n, prolong_mats<V>(ctx), static_cast<V*>(L.r),
                             static_cast<V*>(C.b), static_cast<V*>(C.r), static_cast<V*>(C.x),
                             C.partial, epi(lev + 1, EPI_MG_BEGIN), s);
-      loop<V>(lev + 1, (const V*)C.A64, s);
+      loop<V>(lev + 1, level_op<V>(C), s);
     }
-    launch_prolong<V, V>(ctx->np, ctx->dim, L.n, C.n, ctx->P64, static_cast<V*>(C.x),
+    launch_prolong<V, V>(ctx->np, ctx->dim, L.n, C.n, prolong_mats<V>(ctx), static_cast<V*>(C.x),
                          static_cast<V*>(L.z), s);                         // z = P z_c
     rm<V>(lev, Aop, static_cast<V*>(L.z), 0, 2, s);
     z = smooth<V>(lev, static_cast<V*>(L.r), s);                           // post-smoother
     rm<V>(lev, Aop, z, 1, 3, s);
     // restart check: r = b - A x on request, then the loop condition of this level
     // (compensated on level 0, where the tolerance can sit near the attainable accuracy)
-    if (lev == 0)
+    if (lev == 0 && std::is_same<V, double>::value)
       launch_residual_dd(ctx->np, ctx->dim, (const double*)Aop, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
                          (const double*)L.x, (double*)L.r, (const double*)L.b, L.partial,
                          epi(lev, EPI_RESTART), 1, s);
@@ -438,14 +451,14 @@ struct Cycle {
     }
     launches += 1;                                                      // r_c = R r
     if (direct)
-      launch_restrict<V, V>(ctx->np, ctx->dim, L.n, C.n, ctx->P64, static_cast<V*>(L.r),
+      launch_restrict<V, V>(ctx->np, ctx->dim, L.n, C.n, prolong_mats<V>(ctx), static_cast<V*>(L.r),
                             static_cast<V*>(C.b), nullptr, nullptr, nullptr, EpiArgs{}, s);
     else if (persistent)
-      launch_restrict<V, V>(ctx->np, ctx->dim, L.n, C.n, ctx->P64, static_cast<V*>(L.r),
+      launch_restrict<V, V>(ctx->np, ctx->dim, L.n, C.n, prolong_mats<V>(ctx), static_cast<V*>(L.r),
                             static_cast<V*>(C.b), static_cast<V*>(C.r), static_cast<V*>(C.x),
                             nullptr, EpiArgs{}, s);
     else
-      launch_restrict<V, V>(ctx->np, ctx->dim, L.n, C.n, ctx->P64, static_cast<V*>(L.r),
+      launch_restrict<V, V>(ctx->np, ctx->dim, L.n, C.n, prolong_mats<V>(ctx), static_cast<V*>(L.r),
                             static_cast<V*>(C.b), static_cast<V*>(C.r), static_cast<V*>(C.x),
                             C.partial, epi(1, EPI_MG_BEGIN), s);
     CK(cudaEventRecord(ctx->fork_ev, s));                                // fork
@@ -463,18 +476,23 @@ struct Cycle {
       launches += 1;
       launch_coarse(ctx, cs);
     } else {
-      loop<V>(1, (const V*)C.A64, cs);
+      loop<V>(1, level_op<V>(C), cs);
     }
     launches += 1;
-    launch_prolong<V, V>(ctx->np, ctx->dim, L.n, C.n, ctx->P64, static_cast<V*>(C.x),
+    launch_prolong<V, V>(ctx->np, ctx->dim, L.n, C.n, prolong_mats<V>(ctx), static_cast<V*>(C.x),
                          reinterpret_cast<V*>(ctx->zc), cs);                // z_cor = P z_c
     CK(cudaEventRecord(ctx->join_ev, cs));                               // join
     CK(cudaStreamWaitEvent(s, ctx->join_ev, 0));
     rm<V>(0, Aop, reinterpret_cast<const V*>(ctx->zc), 1, 2, s);
     launches += 1;                                                       // restart check
-    launch_residual_dd(ctx->np, ctx->dim, (const double*)Aop, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
-                       (const double*)L.x, (double*)L.r, (const double*)L.b, L.partial,
-                       epi(0, EPI_RESTART), 1, s);
+    if (std::is_same<V, double>::value)
+      launch_residual_dd(ctx->np, ctx->dim, (const double*)Aop, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
+                         (const double*)L.x, (double*)L.r, (const double*)L.b, L.partial,
+                         epi(0, EPI_RESTART), 1, s);
+    else
+      launch_spmv<V>(ctx->np, ctx->dim, Aop, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
+                     static_cast<V*>(L.x), static_cast<V*>(L.r), static_cast<V*>(L.b), L.partial,
+                     epi(0, EPI_RESTART), 1, s);
   }
 
   long long body_launches = 0;                        // level-0 loop body (capture)
@@ -528,7 +546,8 @@ struct Cycle {
     CK(cudaStreamEndCapture(bs, nullptr));
   }
 
-  // level 0: r0 = b - A x0 with the FP64 operator, then the level-0 loop
+  // level 0: r0 = b - A x0 (compensated FP64; FP32 in the inner solve of the
+  // iterative-refinement forms), then the level-0 loop
   void run(cudaStream_t s) {
     Level& L = ctx->lv[0];
     if (capture) {
@@ -541,10 +560,15 @@ struct Cycle {
       CK(cudaStreamGetCaptureInfo(s, &cs, &id, &g, &deps, &ed, &nd));
       CK(cudaGraphConditionalHandleCreate(&handle[0], g, 0, 0));
     }
-    launch_residual_dd(ctx->np, ctx->dim, L.A64, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
-                       static_cast<double*>(L.x), static_cast<double*>(L.r), static_cast<double*>(L.b),
-                       L.partial, epi(0, EPI_MG_BEGIN), 0, s);
-    loop<T0>(0, (const T0*)L.A64, s);
+    if (std::is_same<T0, double>::value)
+      launch_residual_dd(ctx->np, ctx->dim, L.A64, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
+                         static_cast<double*>(L.x), static_cast<double*>(L.r), static_cast<double*>(L.b),
+                         L.partial, epi(0, EPI_MG_BEGIN), 0, s);
+    else
+      launch_spmv<T0>(ctx->np, ctx->dim, level_op<T0>(L), L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
+                      static_cast<T0*>(L.x), static_cast<T0*>(L.r), static_cast<T0*>(L.b), L.partial,
+                      epi(0, EPI_MG_BEGIN), 0, s);
+    loop<T0>(0, level_op<T0>(L), s);
   }
 };
 
@@ -552,6 +576,8 @@ template <> const double* Cycle<double, double>::Ainner(const Level& L) const { 
 template <> const float* Cycle<double, float>::Ainner(const Level& L) const { return L.A32; }
 template <> const double* Cycle<double, double>::Pm() const { return ctx->P64; }
 template <> const float* Cycle<double, float>::Pm() const { return ctx->P32; }
+template <> const float* Cycle<float, float>::Ainner(const Level& L) const { return L.A32; }
+template <> const float* Cycle<float, float>::Pm() const { return ctx->P32; }
 
 // host copy of the level states before a cycle
 void init_states(kcmg_ctx* ctx, double rtol0, double atol0, int maxit0) {
@@ -584,11 +610,11 @@ void init_states(kcmg_ctx* ctx, double rtol0, double atol0, int maxit0) {
   CK(cudaStreamSynchronize(ctx->s));
 }
 
-template <typename T>
+template <typename T0, typename T>
 void run_cycle(kcmg_ctx* ctx) {
   if (ctx->p.use_graph) {
     if (!ctx->graph_ready) {
-      Cycle<double, T> cy{ctx};
+      Cycle<T0, T> cy{ctx};
       cy.capture = true;
       ctx->graph_body_launches = 0;
       cudaGraph_t g;
@@ -611,7 +637,7 @@ void run_cycle(kcmg_ctx* ctx) {
     CK(cudaGraphLaunch(ctx->gexec, ctx->s));
     ctx->last_launches = -2;   // filled from the cycle count after the solve
   } else {
-    Cycle<double, T> cy{ctx};
+    Cycle<T0, T> cy{ctx};
     cy.launches = 1;           // the initial residual
     cy.run(ctx->s);
     ctx->last_launches = cy.launches;
@@ -647,6 +673,14 @@ void read_states(kcmg_ctx* ctx, StateReport& rep) {
   CK(cudaStreamSynchronize(ctx->s));
 }
 
+// kernels of one run of the cycle, from the loop-body counts and the executed bodies
+long long cycle_launches(const kcmg_ctx* ctx, const StateReport& rep) {
+  if (ctx->last_launches != -2) return ctx->last_launches + 1;
+  long long n = 2;                  // initial and final residual
+  for (int l = 0; l < ctx->nlev; ++l) n += (long long)rep.st[l].guard * ctx->graph_body_kernels[l];
+  return n;
+}
+
 void fill_info(kcmg_ctx* ctx, kcmg_info* info, const StateReport& rep, double res0, double rel) {
   if (!info) return;
   info->iters = rep.st[0].iters_total;
@@ -657,12 +691,7 @@ void fill_info(kcmg_ctx* ctx, kcmg_info* info, const StateReport& rep, double re
   info->refinements = ctx->mixed ? rep.st[0].nrestart + 1 : 0;
   info->res0 = res0;
   info->rel_res = rel;
-  if (ctx->last_launches == -2) {   // graph: begin + sum over levels of bodies x kernels
-    long long n = 2;                  // initial and final residual
-    for (int l = 0; l < ctx->nlev; ++l) n += (long long)rep.st[l].guard * ctx->graph_body_kernels[l];
-    info->kernel_launches = n;
-  } else
-    info->kernel_launches = ctx->last_launches + 1;
+  info->kernel_launches = cycle_launches(ctx, rep);
   const int hl = rep.st[0].hist_len;
   info->hist_len = 0;
   if (info->hist && info->hist_type && info->hist_cap > 0) {
@@ -676,16 +705,95 @@ void fill_info(kcmg_ctx* ctx, kcmg_info* info, const StateReport& rep, double re
   }
 }
 
+// FP64 iterative refinement around the FP32 inner K-cycle (KCMG_IR32, KCMG_IR32_BF16INV).
+// Outer step: r = b - A x with the FP64 operator (compensated sums); stop when
+// ||r|| <= max(rtol ||r0||, atol); else solve A e = r / ||r|| by the K-cycle in FP32 to
+// the inner tolerance (level 0 from e = 0, empty basis) and take x + ||r|| e if that lowers
+// the FP64 residual.  A step that does not is discarded and ends the solve, so x is never
+// worse than x0.
+kcmg_status solve_ir(kcmg_ctx* ctx, const double* b, double* x, double rtol, double atol,
+                     int maxiter, kcmg_info* info) {
+  Level& L = ctx->lv[0];
+  const size_t N = L.N;
+  copy_in(ctx, ctx->bo, b, N);
+  copy_in(ctx, ctx->xo, x, N);
+  double rn = fp64_residual(ctx, ctx->xo, ctx->bo, ctx->ro);
+  const double r0 = rn;
+  const double eps = fmax(rtol * r0, atol);
+  std::vector<double> hist(1, rn);
+  std::vector<int> htype(1, 0);
+  StateReport rep;
+  int cycles = 0, steps = 0, restarts = 0, status = KCMG_OK;
+  int lit[KCMG_MAX_LEVELS] = {0};
+  long long launches = 1;
+  while (std::isfinite(rn) && rn > eps && cycles < maxiter && steps < ctx->p.ir_max_steps) {
+    launch_scale_to_float(ctx->ro, static_cast<float*>(L.b), 1.0 / rn, N, ctx->s);   // inner b
+    CK(cudaMemsetAsync(L.x, 0, N * sizeof(float), ctx->s));                          // inner x0
+    init_states(ctx, ctx->p.ir_inner_rtol, 0.0, std::min(maxiter - cycles, ctx->p.ir_inner_maxit));
+    run_cycle<float, float>(ctx);
+    read_states(ctx, rep);
+    if (ctx->coarse_kernel) {
+      int bar_err = 0;
+      CK(cudaMemcpyAsync(&bar_err, ctx->cc.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+      CK(cudaStreamSynchronize(ctx->s));
+      if (bar_err) {
+        set_err(ctx, "coarse cycle: a grid barrier timed out; the result is invalid");
+        return KCMG_CUDA_ERROR;
+      }
+    }
+    cycles += rep.st[0].iters_total;
+    restarts += rep.st[0].nrestart;
+    for (int l = 0; l < ctx->nlev; ++l) lit[l] += rep.st[l].iters_total;
+    launches += cycle_launches(ctx, rep) + 3;   // + inner b, update, FP64 residual
+    ++steps;
+    if (rep.st[0].status != KCMG_OK) {          // breakdown or non-finite inner iterate
+      status = rep.st[0].status;
+      break;
+    }
+    // trial x_t = x + ||r|| e and its FP64 residual (into ro)
+    CK(cudaMemcpyAsync(ctx->xt, ctx->xo, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->s));
+    launch_axpy_scaled_to_double(static_cast<const float*>(L.x), ctx->xt, rn, N, ctx->s);
+    const double rt = fp64_residual(ctx, ctx->xt, ctx->bo, ctx->ro);
+    if (!(rt < rn)) break;                      // no progress: keep x, stop
+    std::swap(ctx->xo, ctx->xt);
+    rn = rt;
+    hist.push_back(rn);
+    htype.push_back(6);
+  }
+  copy_out(ctx, x, ctx->xo, N);
+  CK(cudaStreamSynchronize(ctx->s));
+  if (info) {
+    info->iters = cycles;
+    for (int l = 0; l < KCMG_MAX_LEVELS; ++l) info->level_iters[l] = l < ctx->nlev ? lit[l] : 0;
+    info->restarts = restarts;
+    info->refinements = steps;
+    info->res0 = r0;
+    info->rel_res = r0 > 0 ? rn / r0 : 0.0;
+    info->kernel_launches = launches;
+    info->hist_len = 0;
+    if (info->hist && info->hist_type && info->hist_cap > 0) {
+      const int m = std::min<int>((int)hist.size(), info->hist_cap);
+      CK(cudaMemcpy(info->hist, hist.data(), m * sizeof(double), cudaMemcpyDefault));
+      CK(cudaMemcpy(info->hist_type, htype.data(), m * sizeof(int), cudaMemcpyDefault));
+      info->hist_len = m;
+    }
+  }
+  if (status != KCMG_OK) return (kcmg_status)status;
+  if (!std::isfinite(rn)) return KCMG_NONFINITE;
+  return (rn <= eps) ? KCMG_OK : KCMG_NOT_CONVERGED;
+}
+
 kcmg_status solve_impl(kcmg_ctx* ctx, const double* b, double* x, double rtol, double atol,
                        int maxiter, kcmg_info* info) {
+  if (ctx->ir) return solve_ir(ctx, b, x, rtol, atol, maxiter, info);
   Level& L = ctx->lv[0];
   const size_t N = L.N;
   StateReport rep;
   copy_in(ctx, static_cast<double*>(L.b), b, N);
   copy_in(ctx, static_cast<double*>(L.x), x, N);
   init_states(ctx, rtol, atol, maxiter);
-  if (ctx->mixed) run_cycle<float>(ctx);
-  else run_cycle<double>(ctx);
+  if (ctx->mixed) run_cycle<double, float>(ctx);
+  else run_cycle<double, double>(ctx);
   read_states(ctx, rep);
   if (ctx->coarse_kernel) {
     int bar_err = 0;
@@ -768,6 +876,9 @@ void kcmg_default_params(kcmg_params* p, int dim, int np, const int n[3], int nl
   p->precision = KCMG_FP64;
   p->use_graph = 1;
   p->coarse_persistent = 1;
+  p->ir_inner_rtol = 1e-3;
+  p->ir_max_steps = 64;
+  p->ir_inner_maxit = 300;
 }
 
 const char* kcmg_status_string(kcmg_status s) {
@@ -832,7 +943,12 @@ kcmg_ctx* build_ctx(const kcmg_params* p, cudaStream_t user, const double* block
     REQUIRE(p->nlevels >= 2 && p->nlevels <= KCMG_MAX_LEVELS, "nlevels must be in [2, %d]", KCMG_MAX_LEVELS);
     REQUIRE(p->blocks && p->prolong, "blocks and prolong must be set");
     REQUIRE(p->sweeps >= 1 && p->sweeps <= 64, "sweeps must be in [1, 64]");
-    REQUIRE(p->precision >= 0 && p->precision <= 2, "unknown precision %d", p->precision);
+    REQUIRE(p->precision >= 0 && p->precision <= KCMG_IR32_BF16INV, "unknown precision %d", p->precision);
+    if (p->precision >= KCMG_IR32) {
+      REQUIRE(p->ir_inner_rtol > 0.0 && p->ir_inner_rtol < 1.0, "ir_inner_rtol must be in (0, 1)");
+      REQUIRE(p->ir_max_steps >= 1, "ir_max_steps must be >= 1");
+      REQUIRE(p->ir_inner_maxit >= 1, "ir_inner_maxit must be >= 1");
+    }
     for (int j = 0; j < p->dim; ++j)
       REQUIRE(p->n[j] > 0 && p->n[j] % (1 << (p->nlevels - 1)) == 0,
               "n[%d] = %d is not divisible by 2^(nlevels-1)", j, p->n[j]);
@@ -844,6 +960,7 @@ kcmg_ctx* build_ctx(const kcmg_params* p, cudaStream_t user, const double* block
     ctx->nlev = p->nlevels;
     ctx->nch = 1 << p->dim;
     ctx->mixed = p->precision != KCMG_FP64;
+    ctx->ir = p->precision >= KCMG_IR32;
     ctx->user = user;
     int dev = 0;
     CK(cudaGetDevice(&dev));
@@ -887,12 +1004,13 @@ kcmg_ctx* build_ctx(const kcmg_params* p, cudaStream_t user, const double* block
       if (l == 0) {
         size_t fr = 0, tot = 0;
         CK(cudaMemGetInfo(&fr, &tot));
-        const size_t per = (size_t)2 * ctx->lv[0].N * sizeof(double);
+        const size_t per = (size_t)2 * ctx->lv[0].N * (ctx->ir ? sizeof(float) : sizeof(double));
         while (cap > 16 && (size_t)cap * per > fr / 3) cap /= 2;
         if (cap < per_cycle0 + 3) cap = per_cycle0 + 3;   // one cycle must always fit
       }
-      alloc_cycle_vectors<double>(ctx, ctx->lv[l], cap);
-      if (ctx->mixed) {   // FP32 smoother buffers
+      if (ctx->ir) alloc_cycle_vectors<float>(ctx, ctx->lv[l], cap);
+      else alloc_cycle_vectors<double>(ctx, ctx->lv[l], cap);
+      if (ctx->mixed) {   // FP32 smoother buffers (and FP32 scratch of the component calls)
         Level& Lm = ctx->lv[l];
         Lm.r_lo = dalloc<float>(ctx, Lm.N);
         Lm.z_lo = dalloc<float>(ctx, Lm.N);
@@ -901,7 +1019,7 @@ kcmg_ctx* build_ctx(const kcmg_params* p, cudaStream_t user, const double* block
     }
     {  // coarsest level: b (restricted residual) and x (direct solution) only
       Level& C = ctx->lv[ctx->nlev - 1];
-      C.b = dalloc<double>(ctx, C.N);
+      C.b = dalloc<double>(ctx, C.N);   // FP32 vectors of the inner solve fit as well
       C.x = dalloc<double>(ctx, C.N);
     }
     // persistent coarse cycle for levels >= 1 (needs at least one iterated coarse level)
@@ -924,9 +1042,12 @@ kcmg_ctx* build_ctx(const kcmg_params* p, cudaStream_t user, const double* block
       int grid = 0;
       const int thr = ctx->lv[ctx->cc_lev0].block_rows;
       cudaError_t ge;
-      if (!ctx->mixed) ge = coarse_cycle_grid<double, double>(ctx->np, ctx->dim, thr, &grid);
-      else if (p->precision == KCMG_MIXED_BF16INV) ge = coarse_cycle_grid<float, __nv_bfloat16>(ctx->np, ctx->dim, thr, &grid);
-      else ge = coarse_cycle_grid<float, float>(ctx->np, ctx->dim, thr, &grid);
+      const bool bf16 = p->precision == KCMG_MIXED_BF16INV || p->precision == KCMG_IR32_BF16INV;
+      if (!ctx->mixed) ge = coarse_cycle_grid<double, double, double>(ctx->np, ctx->dim, thr, &grid);
+      else if (ctx->ir && bf16) ge = coarse_cycle_grid<float, float, __nv_bfloat16>(ctx->np, ctx->dim, thr, &grid);
+      else if (ctx->ir) ge = coarse_cycle_grid<float, float, float>(ctx->np, ctx->dim, thr, &grid);
+      else if (bf16) ge = coarse_cycle_grid<double, float, __nv_bfloat16>(ctx->np, ctx->dim, thr, &grid);
+      else ge = coarse_cycle_grid<double, float, float>(ctx->np, ctx->dim, thr, &grid);
       CK(ge);
       if (const char* ev = getenv("KCMG_COARSE_GRID")) {   // tuning override, capped at residency
         const int g = atoi(ev);
@@ -954,11 +1075,12 @@ kcmg_ctx* build_ctx(const kcmg_params* p, cudaStream_t user, const double* block
       for (int l = 1; l < ctx->nlev; ++l) {
         Level& L = ctx->lv[l];
         CoarseLevel& c = a.lv[l];
-        c.A = L.A64;                                                  // Alg. 1 operator
+        c.A = ctx->ir ? (const void*)L.A32 : (const void*)L.A64;      // Alg. 1 operator
         c.As = ctx->mixed ? (const void*)L.A32 : (const void*)L.A64;  // smoother operator
         c.Dinv = !ctx->mixed ? (const void*)L.D64 : L.D16 ? (const void*)L.D16 : (const void*)L.D32;
-        c.s0 = ctx->mixed ? (void*)L.z_lo : L.t;                      // smoother scratch
-        c.s1 = ctx->mixed ? (void*)L.t_lo : L.wre;
+        const bool lo = ctx->mixed && !ctx->ir;                       // FP64 vectors, FP32 sweeps
+        c.s0 = lo ? (void*)L.z_lo : L.t;                              // smoother scratch
+        c.s1 = lo ? (void*)L.t_lo : L.wre;
         c.nbr = L.nbr;
         for (int j = 0; j < 3; ++j) c.n[j] = L.n[j];
         c.N = L.N;
@@ -989,10 +1111,15 @@ kcmg_ctx* build_ctx(const kcmg_params* p, cudaStream_t user, const double* block
       a.stat_launches = ctx->stat_launches;
       a.stat_bytes = ctx->stat_bytes;
       a.smoother_bytes = ctx->mixed ? 4 : 8;
-      a.inverse_bytes = !ctx->mixed ? 8 : (p->precision == KCMG_MIXED_BF16INV ? 2 : 4);
+      a.inverse_bytes = !ctx->mixed ? 8 : (bf16 ? 2 : 4);
     }
     const size_t N0 = ctx->lv[0].N;
     ctx->ro = dalloc<double>(ctx, N0);
+    if (ctx->ir) {   // FP64 vectors of the outer refinement loop
+      ctx->xo = dalloc<double>(ctx, N0);
+      ctx->bo = dalloc<double>(ctx, N0);
+      ctx->xt = dalloc<double>(ctx, N0);
+    }
     if (p->async_smooth > 0) ctx->zc = dalloc<double>(ctx, N0);
     ctx->hist = dalloc<double>(ctx, ctx->hist_cap);
     ctx->hist_type = dalloc<int>(ctx, ctx->hist_cap);
@@ -1013,8 +1140,9 @@ kcmg_ctx* build_ctx(const kcmg_params* p, cudaStream_t user, const double* block
   }
 }
 
-// vectors of every level are FP64 (only the smoother sweeps use the inner precision)
-bool level_is_f32(const kcmg_ctx*, int) { return false; }
+// vectors of every level are FP64 (the mixed forms use FP32 only in the smoother sweeps),
+// or FP32 in the inner solve of the iterative-refinement forms
+bool level_is_f32(const kcmg_ctx* ctx, int) { return ctx->ir; }
 
 // FP64 user vector -> level buffer of the level's type
 void load_vec(kcmg_ctx* ctx, int lev, void* dst, const double* src, size_t n) {
@@ -1093,6 +1221,7 @@ kcmg_status kcmg_solve(kcmg_ctx* ctx, const double* b, double* x, int nrhs, doub
     REQUIRE(b && x, "b and x must be non-null");
     REQUIRE(nrhs >= 1 && nrhs <= kMaxRhs, "nrhs must be in [1, %d]", kMaxRhs);
     REQUIRE(rtol >= 0 && atol >= 0 && maxiter >= 0, "negative tolerance or maxiter");
+    REQUIRE(nrhs == 1 || !ctx->ir, "batched solves (nrhs > 1) support the FP64 and mixed forms");
     if (nrhs > 1) return solve_multi(ctx, b, x, nrhs, rtol, atol, maxiter, info);
     return solve_impl(ctx, b, x, rtol, atol, maxiter, info);
   });
@@ -1104,6 +1233,7 @@ kcmg_status kcmg_solve_adjoint(kcmg_ctx* ctx, const double* g, double* lambda, i
     REQUIRE(g && lambda, "g and lambda must be non-null");
     REQUIRE(nrhs >= 1 && nrhs <= kMaxRhs, "nrhs must be in [1, %d]", kMaxRhs);
     REQUIRE(rtol >= 0 && atol >= 0 && maxiter >= 0, "negative tolerance or maxiter");
+    REQUIRE(nrhs == 1 || !ctx->ir, "batched solves (nrhs > 1) support the FP64 and mixed forms");
     kcmg_status st = ensure_adjoint(ctx);
     if (st != KCMG_OK) return st;
     kcmg_ctx* a = ctx->adj;
@@ -1127,7 +1257,7 @@ kcmg_status kcmg_apply(kcmg_ctx* ctx, int level, int op, const double* x, double
                           ctx->stage_in, ctx->stage_out, nullptr, nullptr, none, 0, ctx->s);
     } else {
       float* xi = ctx->lv[0].r_lo;    // FP32 scratch of the finest size
-      float* yi = ctx->lv[0].z_lo;
+      float* yi = ctx->lv[0].z_lo;     // (the inner-precision operator of the mixed forms)
       launch_convert<double, float>(ctx->stage_in, xi, L.N, ctx->s);
       launch_spmv<float>(ctx->np, ctx->dim, L.A32, L.nbr, L.N, L.G, L.rows_pad, L.block_rows, xi,
                          yi, nullptr, nullptr, none, 0, ctx->s);
@@ -1146,7 +1276,10 @@ kcmg_status kcmg_smooth(kcmg_ctx* ctx, int level, const double* r, double* z) {
     Level& L = ctx->lv[level];
     load_vec(ctx, level, L.b, r, L.N);
     const void* out;
-    if (ctx->mixed) {
+    if (ctx->ir) {
+      Cycle<float, float> cy{ctx};
+      out = cy.smooth<float>(level, static_cast<float*>(L.b), ctx->s);
+    } else if (ctx->mixed) {
       Cycle<double, float> cy{ctx};
       out = cy.smooth<double>(level, static_cast<double*>(L.b), ctx->s);
     } else {
@@ -1164,8 +1297,12 @@ kcmg_status kcmg_restrict(kcmg_ctx* ctx, int level, const double* r, double* rc)
     REQUIRE(level >= 0 && level < ctx->nlev - 1 && r && rc, "bad level or null vector");
     Level &L = ctx->lv[level], &C = ctx->lv[level + 1];
     load_vec(ctx, level, L.t, r, L.N);
-    launch_restrict<double, double>(ctx->np, ctx->dim, L.n, C.n, ctx->P64, static_cast<double*>(L.t),
-                                    static_cast<double*>(C.b), nullptr, nullptr, nullptr, EpiArgs{}, ctx->s);
+    if (ctx->ir)
+      launch_restrict<float, float>(ctx->np, ctx->dim, L.n, C.n, ctx->P32, static_cast<float*>(L.t),
+                                    static_cast<float*>(C.b), nullptr, nullptr, nullptr, EpiArgs{}, ctx->s);
+    else
+      launch_restrict<double, double>(ctx->np, ctx->dim, L.n, C.n, ctx->P64, static_cast<double*>(L.t),
+                                      static_cast<double*>(C.b), nullptr, nullptr, nullptr, EpiArgs{}, ctx->s);
     CK(cudaGetLastError());
     store_vec(ctx, level + 1, rc, C.b, C.N);
     return KCMG_OK;
@@ -1177,8 +1314,12 @@ kcmg_status kcmg_prolong(kcmg_ctx* ctx, int level, const double* zc, double* z) 
     REQUIRE(level >= 0 && level < ctx->nlev - 1 && zc && z, "bad level or null vector");
     Level &L = ctx->lv[level], &C = ctx->lv[level + 1];
     load_vec(ctx, level + 1, C.x, zc, C.N);
-    launch_prolong<double, double>(ctx->np, ctx->dim, L.n, C.n, ctx->P64, static_cast<double*>(C.x),
-                                   static_cast<double*>(L.t), ctx->s);
+    if (ctx->ir)
+      launch_prolong<float, float>(ctx->np, ctx->dim, L.n, C.n, ctx->P32, static_cast<float*>(C.x),
+                                   static_cast<float*>(L.t), ctx->s);
+    else
+      launch_prolong<double, double>(ctx->np, ctx->dim, L.n, C.n, ctx->P64, static_cast<double*>(C.x),
+                                     static_cast<double*>(L.t), ctx->s);
     CK(cudaGetLastError());
     store_vec(ctx, level, z, L.t, L.N);
     return KCMG_OK;
@@ -1214,7 +1355,7 @@ template <typename T0, typename T, typename V>
 void rm_sequence_impl(kcmg_ctx* ctx, int level, const double* z, int ncorr) {
   Level& L = ctx->lv[level];
   Cycle<T0, T> cy{ctx};
-  const V* Aop = (const V*)L.A64;
+  const V* Aop = level_op<V>(L);
   launch_spmv<V>(ctx->np, ctx->dim, Aop, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
                  static_cast<V*>(L.x), static_cast<V*>(L.r), static_cast<V*>(L.b), L.partial,
                  cy.epi(level, EPI_MG_BEGIN), 0, ctx->s);
@@ -1237,7 +1378,8 @@ kcmg_status kcmg_rm_sequence(kcmg_ctx* ctx, int level, const double* b, const do
     init_states(ctx, 0.0, 0.0, 1 << 30);
     load_vec(ctx, level, L.b, b, L.N);
     load_vec(ctx, level, L.x, x0, L.N);
-    if (!ctx->mixed) rm_sequence_impl<double, double, double>(ctx, level, z, ncorr);
+    if (ctx->ir) rm_sequence_impl<float, float, float>(ctx, level, z, ncorr);
+    else if (!ctx->mixed) rm_sequence_impl<double, double, double>(ctx, level, z, ncorr);
     else rm_sequence_impl<double, float, double>(ctx, level, z, ncorr);
     CK(cudaGetLastError());
     store_vec(ctx, level, x, L.x, L.N);
@@ -1254,6 +1396,7 @@ kcmg_status kcmg_apply_multi(kcmg_ctx* ctx, int level, int nrhs, const double* x
   return guarded(ctx, [&]() -> kcmg_status {
     REQUIRE(level >= 0 && level < ctx->nlev - 1 && x && y, "bad level or null vector");
     REQUIRE(nrhs >= 2 && nrhs <= kMaxRhs, "nrhs must be in [2, %d]", kMaxRhs);
+    REQUIRE(!ctx->ir, "batched calls support the FP64 and mixed forms");
     kcmg_status st = mrhs_ensure(&ctx->mrhs, mrhs_view(ctx), nrhs, &ctx->err);
     if (st != KCMG_OK) return st;
     return mrhs_apply(ctx->mrhs, level, x, y);
@@ -1264,6 +1407,7 @@ kcmg_status kcmg_smooth_multi(kcmg_ctx* ctx, int level, int nrhs, const double* 
   return guarded(ctx, [&]() -> kcmg_status {
     REQUIRE(level >= 0 && level < ctx->nlev - 1 && r && z, "bad level or null vector");
     REQUIRE(nrhs >= 2 && nrhs <= kMaxRhs, "nrhs must be in [2, %d]", kMaxRhs);
+    REQUIRE(!ctx->ir, "batched calls support the FP64 and mixed forms");
     kcmg_status st = mrhs_ensure(&ctx->mrhs, mrhs_view(ctx), nrhs, &ctx->err);
     if (st != KCMG_OK) return st;
     return mrhs_smooth(ctx->mrhs, level, r, z);
@@ -1314,20 +1458,27 @@ kcmg_status kcmg_kernel_report(kcmg_ctx* ctx, int reps, double* out, int nout) {
       cudaEvent_t e0, e1;
       CK(cudaEventCreate(&e0));
       CK(cudaEventCreate(&e1));
-      CK(cudaMemsetAsync(L.b, 0, L.N * sizeof(double), ctx->s));
-      CK(cudaMemsetAsync(L.t, 0, L.N * sizeof(double), ctx->s));
+      const size_t vb = ctx->ir ? sizeof(float) : sizeof(double);   // level vector element
+      CK(cudaMemsetAsync(L.b, 0, L.N * vb, ctx->s));
+      CK(cudaMemsetAsync(L.t, 0, L.N * vb, ctx->s));
       EpiArgs none;
-      // FP64 operator (Alg. 1 SpMV on level 0)
+      // the operator of the level-0 residual minimisation (Alg. 1 SpMV): FP64, or FP32 in
+      // the inner solve of the iterative-refinement forms
       CK(cudaEventRecord(e0, ctx->s));
-      for (int k = 0; k < reps; ++k)
-        launch_spmv<double>(np, ctx->dim, L.A64, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
-                            static_cast<double*>(L.t), static_cast<double*>(L.w), nullptr, nullptr, none, 0, ctx->s);
+      for (int k = 0; k < reps; ++k) {
+        if (ctx->ir)
+          launch_spmv<float>(np, ctx->dim, L.A32, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
+                             static_cast<float*>(L.t), static_cast<float*>(L.w), nullptr, nullptr, none, 0, ctx->s);
+        else
+          launch_spmv<double>(np, ctx->dim, L.A64, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
+                              static_cast<double*>(L.t), static_cast<double*>(L.w), nullptr, nullptr, none, 0, ctx->s);
+      }
       CK(cudaEventRecord(e1, ctx->s));
       CK(cudaEventSynchronize(e1));
       float ms = 0;
       CK(cudaEventElapsedTime(&ms, e0, e1));
       out[3] = ms / reps;
-      out[4] = (double)S * L.N * np * 8 + 2.0 * L.N * 8;
+      out[4] = (double)S * L.N * np * vb + 2.0 * L.N * vb;
       // one full block-Jacobi sweep on level 0 in the smoother's precision
       const double sb = ctx->mixed ? 4 : 8;
       const double ib = !ctx->mixed ? 8 : (L.D16 ? 2 : 4);

@@ -122,6 +122,9 @@ template <typename Ts, typename Td>
 void launch_convert(const Ts* src, Td* dst, size_t n, cudaStream_t s);
 template <typename T>
 void launch_axpy_to_double(const T* e, double* x, size_t n, cudaStream_t s); // x += e
+// iterative refinement: dst = (float)(a * src); x += a * (double)e
+void launch_scale_to_float(const double* src, float* dst, double a, size_t n, cudaStream_t s);
+void launch_axpy_scaled_to_double(const float* e, double* x, double a, size_t n, cudaStream_t s);
 
 // setup kernels (FP64, natural layout [S][C][np][np])
 int launch_galerkin(int np, int dim, const double* Af, const int* nbrf, const int* nf,
@@ -161,7 +164,7 @@ enum CoarsePhase : int {
 };
 
 struct CoarseLevel {
-  const void* A;        // row-interleaved FP64 operator (residual minimisation)
+  const void* A;        // row-interleaved operator of the residual minimisation (vector type)
   const void* As;       // row-interleaved operator of the smoother (its precision)
   const void* Dinv;     // row-interleaved block inverses (smoother precision or BF16)
   void *s0, *s1;        // smoother scratch vectors (smoother precision)
@@ -177,7 +180,7 @@ struct CoarseLevel {
 struct CoarseArgs {
   CoarseLevel lv[KCMG_MAX_LEVELS];
   int lev0, nlev, dim, np;
-  const void* P;               // prolongation matrices (FP64)
+  const void* P;               // prolongation matrices (FP64; the kernel converts them)
   const double* Ainv;          // dense inverse of the coarsest operator
   int Nc;
   double omega;
@@ -199,9 +202,10 @@ struct CoarseArgs {
   int inverse_bytes;           // bytes per element of the stored block inverses
 };
 
-template <typename T, typename TI>
+// TV: vectors, bases and the residual minimisation; T: smoother sweeps; TI: stored inverses
+template <typename TV, typename T, typename TI>
 cudaError_t coarse_cycle_grid(int np, int dim, int threads, int* grid);
-template <typename T, typename TI>
+template <typename TV, typename T, typename TI>
 cudaError_t launch_coarse_cycle(const CoarseArgs& a, int grid, int threads, cudaStream_t s);
 
 // finest-level FP64 operator of a context, for the no-allocation residual (noalloc.cu)

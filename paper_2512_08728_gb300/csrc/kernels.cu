@@ -453,18 +453,23 @@ k_gram_dots(const T* __restrict__ W, int N, const T* __restrict__ w, double* par
   const int chunk = (N + gridDim.x - 1) / gridDim.x;
   const int j0 = blockIdx.x * chunk, j1 = min(N, j0 + chunk);
   for (int c0 = 0; c0 < ncol; c0 += 8) {
-    double acc[8];
+    // each thread sums its few elements in T (FP32 vectors: FP32 products and partial
+    // sums, no per-element FP64 work); the block and grid reductions are FP64
+    T acct[8];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc[c] = 0.0;
+    for (int c = 0; c < 8; ++c) acct[c] = T(0);
     for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-      const double wv = (double)w[j];
+      const T wv = w[j];
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         const int col = c0 + c;
-        if (col < l) acc[c] = fma((double)__ldg(W + (size_t)col * N + j), wv, acc[c]);
-        else if (col == l) acc[c] = fma(wv, wv, acc[c]);
+        if (col < l) acct[c] = fma(__ldg(W + (size_t)col * N + j), wv, acct[c]);
+        else if (col == l) acct[c] = fma(wv, wv, acct[c]);
       }
     }
+    double acc[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = (double)acct[c];
     bsum_n<8>(acc, sh);
     if (threadIdx.x == 0)
 #pragma unroll
@@ -528,7 +533,7 @@ k_gram_update(T* W, T* Z, int N, const T* __restrict__ w, const T* __restrict__ 
   const T* ws = re ? wre : w;
   T* Wl = W + (size_t)l * N;
   T* Zl = Z + (size_t)l * N;
-  double nw2 = 0.0, wr = 0.0;
+  T nw2 = T(0), wr = T(0);   // per-thread sums in T, reduced in FP64
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
     T a = ws[j], c = z[j];
 #pragma unroll 4
@@ -538,10 +543,10 @@ k_gram_update(T* W, T* Z, int N, const T* __restrict__ w, const T* __restrict__ 
     }
     Wl[j] = a;
     Zl[j] = c;
-    nw2 = fma((double)a, (double)a, nw2);
-    wr = fma((double)a, (double)r[j], wr);
+    nw2 = fma(a, a, nw2);
+    wr = fma(a, r[j], wr);
   }
-  double v[2] = {nw2, wr};
+  double v[2] = {(double)nw2, (double)wr};
   finish_reduction<2>(v, partial, e, sh);
 }
 
@@ -593,6 +598,15 @@ template <typename Ts, typename Td>
 __global__ void k_convert(const Ts* __restrict__ a, Td* __restrict__ b, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     b[i] = (Td)a[i];
+}
+__global__ void k_scale_to_float(const double* __restrict__ a, float* __restrict__ b, double s, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    b[i] = (float)(s * a[i]);
+}
+__global__ void k_axpy_scaled_to_double(const float* __restrict__ e, double* __restrict__ x, double s,
+                                        size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    x[i] = fma(s, (double)e[i], x[i]);
 }
 template <typename T>
 __global__ void k_axpy_to_double(const T* __restrict__ e, double* __restrict__ x, size_t n) {
@@ -1048,6 +1062,12 @@ void launch_convert(const Ts* src, Td* dst, size_t n, cudaStream_t s) {
 template <typename T>
 void launch_axpy_to_double(const T* e, double* x, size_t n, cudaStream_t s) {
   k_axpy_to_double<T><<<nblocks(n, 256), 256, 0, s>>>(e, x, n);
+}
+void launch_scale_to_float(const double* src, float* dst, double a, size_t n, cudaStream_t s) {
+  k_scale_to_float<<<nblocks(n, 256), 256, 0, s>>>(src, dst, a, n);
+}
+void launch_axpy_scaled_to_double(const float* e, double* x, double a, size_t n, cudaStream_t s) {
+  k_axpy_scaled_to_double<<<nblocks(n, 256), 256, 0, s>>>(e, x, a, n);
 }
 
 int launch_galerkin(int np, int dim, const double* Af, const int* nbrf, const int* nf,

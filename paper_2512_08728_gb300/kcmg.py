@@ -17,8 +17,9 @@ from .build import LIB
 KCMG_MAX_LEVELS = 12
 KCMG_OK, KCMG_NOT_CONVERGED, KCMG_BREAKDOWN, KCMG_NONFINITE, KCMG_SINGULAR, \
     KCMG_INVALID_ARG, KCMG_OOM, KCMG_CUDA_ERROR = range(8)
-KCMG_FP64, KCMG_MIXED, KCMG_MIXED_BF16INV = range(3)
-PRECISIONS = {"fp64": KCMG_FP64, "mixed": KCMG_MIXED, "mixed_bf16": KCMG_MIXED_BF16INV}
+KCMG_FP64, KCMG_MIXED, KCMG_MIXED_BF16INV, KCMG_IR32, KCMG_IR32_BF16INV = range(5)
+PRECISIONS = {"fp64": KCMG_FP64, "mixed": KCMG_MIXED, "mixed_bf16": KCMG_MIXED_BF16INV,
+              "ir32": KCMG_IR32, "ir32_bf16": KCMG_IR32_BF16INV}
 # phase kinds of the coarse-cycle kernel's timers (kcmg_kernel_report out[19 + k])
 COARSE_PHASES = ["sweep", "rm_gram1", "rm_reorth", "rm_update", "rm_finish", "transfer",
                  "coarsest", "restart", "control"]
@@ -30,7 +31,9 @@ class kcmg_params(C.Structure):
                 ("sweeps", C.c_int), ("lvl_rtol", C.c_double * KCMG_MAX_LEVELS),
                 ("lvl_maxit", C.c_int * KCMG_MAX_LEVELS), ("lmax", C.c_int),
                 ("precision", C.c_int), ("use_graph", C.c_int), ("coarse_persistent", C.c_int),
-                ("tc_tf32_only", C.c_int), ("async_smooth", C.c_int)]
+                ("tc_tf32_only", C.c_int), ("async_smooth", C.c_int),
+                ("ir_inner_rtol", C.c_double), ("ir_max_steps", C.c_int),
+                ("ir_inner_maxit", C.c_int)]
 
 
 class kcmg_info(C.Structure):
@@ -331,7 +334,8 @@ class KCycleSolver:
 
     def __init__(self, problem, precision="fp64", use_graph=True, omega=0.7, sweeps=5,
                  lmax=0, lvl_rtol=None, lvl_maxit=None, coarse_persistent=True, stream=None,
-                 tc_tf32_only=0, async_smooth=0):
+                 tc_tf32_only=0, async_smooth=0, ir_inner_rtol=None, ir_max_steps=None,
+                 ir_inner_maxit=None):
         pr = problem
         self.dim, self.np_, self.nlevels = pr.d, pr.np_, pr.nlevels
         self.ndof = pr.ndof
@@ -342,6 +346,12 @@ class KCycleSolver:
         p.coarse_persistent = int(coarse_persistent)
         p.tc_tf32_only = int(tc_tf32_only)
         p.async_smooth = int(async_smooth)
+        if ir_inner_rtol is not None:
+            p.ir_inner_rtol = float(ir_inner_rtol)
+        if ir_max_steps is not None:
+            p.ir_max_steps = int(ir_max_steps)
+        if ir_inner_maxit is not None:
+            p.ir_inner_maxit = int(ir_inner_maxit)
         if lvl_rtol is not None:
             for i, v in enumerate(lvl_rtol):
                 p.lvl_rtol[i] = v

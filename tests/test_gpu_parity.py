@@ -377,3 +377,71 @@ def test_benchmark_level_layout_32cube_task_parallel_matches_oracle(monkeypatch)
         pr.b, rtol=3e-11, maxiter=2000)
     assert io["status"] == 0
     _check_solution(pr, x, info, x_or)
+
+
+# ------------------------------------------------------------------ FP64 refinement, FP32 inner solve
+@pytest.mark.parametrize("name", SMALL + ["ragged_3d_p2", "sipg2d_p1_32x32_5lev"])
+@pytest.mark.parametrize("precision", ["ir32", "ir32_bf16"])
+@pytest.mark.parametrize("m,persistent", [(0, True), (0, False), (3, True)])
+def test_iterative_refinement_solve_matches_fp64_oracle(name, precision, m, persistent):
+    """FP64 outer refinement around a K-cycle run entirely in FP32 (operators, sweeps,
+    transfers, bases) with FP64 Gram reductions and coarsest solve: the FP64 true residual
+    and the distance to the oracle's FP64 solution meet the FP64 bounds."""
+    pr = _problem(name)
+    x_or, _ = OracleSolver.from_problem(pr).solve(pr.b, rtol=1e-10, maxiter=400)
+    s = pkg.KCycleSolver(pr, precision=precision, use_graph=True, coarse_persistent=persistent,
+                         async_smooth=m)
+    x, info = s.solve(pr.b, rtol=1e-10, maxiter=4000)
+    s.close()
+    assert info["status"] == 0, info
+    _check_solution(pr, x, info, x_or)
+    assert info["refinements"] >= 1
+    h, t = info["hist"], info["hist_type"]
+    assert t[0] == 0 and np.all(t[1:] == 6) and len(h) == info["refinements"] + 1
+    assert np.all(np.diff(h) < 0)                 # every accepted step lowers the residual
+
+
+@pytest.mark.parametrize("name", ["sipg2d_p1_16x16", "sipg3d_p2_8cube", "ragged_3d_p2"])
+def test_iterative_refinement_components_in_fp32(name):
+    """The inner solve's kernels on FP32 vectors against the oracle: operator, sweeps,
+    transfers (FP32 rounding), and Alg. 1 on FP32 bases."""
+    pr = _problem(name)
+    orc = OracleSolver.from_problem(pr)
+    s = pkg.KCycleSolver(pr, precision="ir32")
+    rng = np.random.default_rng(7)
+    for lev in range(pr.nlevels - 1):
+        x = rng.standard_normal(orc.ndof(lev))
+        assert _rel(s.apply(lev, x, op=1), orc.apply(lev, x)) < 2e-6
+        assert _rel(s.smooth(lev, x), orc.smooth(lev, x)) < 3e-5
+        zc = rng.standard_normal(orc.ndof(lev + 1))
+        assert _rel(s.restrict(lev, x), orc.restrict(lev, x)) < 2e-6
+        assert _rel(s.prolong(lev, zc), orc.prolong(lev, zc)) < 2e-6
+    x0 = rng.uniform(-1, 1, pr.ndof)
+    orc.rm_begin(0, pr.b, x0)
+    r = pr.b - orc.apply(0, x0)
+    zs = []
+    for k in range(8):
+        z = orc.smooth(0, r) if k % 2 == 0 else orc.prolong(0, orc.restrict(0, r))
+        zs.append(z)
+        _, xo, r, lo = orc.rm_call(0, z)
+    xg, rg, lg = s.rm_sequence(0, pr.b, x0, np.stack(zs))
+    assert lg == lo
+    scale = np.linalg.norm(pr.b - orc.apply(0, x0))
+    assert np.linalg.norm(rg - r) <= 1e-5 * scale
+    s.close()
+
+
+def test_iterative_refinement_degenerate_inputs():
+    pr = workload("sipg2d_p1_16x16").make(0)
+    s = pkg.KCycleSolver(pr, precision="ir32")
+    x, info = s.solve(np.zeros(pr.ndof), rtol=1e-10)          # b = 0: x = 0 at once
+    assert info["status"] == 0 and info["iters"] == 0 and not np.any(x)
+    x, info = s.solve(pr.b, rtol=1e-10, maxiter=0)              # no cycles allowed
+    assert info["status"] == 1 and np.array_equal(x, np.zeros(pr.ndof))
+    xs, _ = s.solve(pr.b, rtol=1e-10)
+    x, info = s.solve(pr.b, x0=xs, rtol=0.0, atol=1e-6)         # x0 already converged
+    assert info["status"] == 0 and info["refinements"] == 0 and np.array_equal(x, xs)
+    with pytest.raises(pkg.KcmgError) as e:                    # batched solves: FP64/mixed only
+        s.solve(np.zeros((pr.ndof, 2)), rtol=1e-10)
+    assert e.value.status == 5
+    s.close()

@@ -436,27 +436,40 @@ struct CoarseCycle {
     return true;
   }
 
-  // partial[blk][c] for c < l: W_c . w ; c = l: ||w||^2
+  // partial[blk][c] for c < l: W_c . w ; c = l: ||w||^2.  Groups of 8 columns; the last
+  // group reads a valid column in place of the missing ones and drops those sums, and the
+  // norm is a separate sum of group 0, so every step issues the same FMAs.  Per-thread
+  // sums in T, block and grid sums in FP64.
   __device__ void dots(const T* W, int N, const T* w, int l, double* part) {
     const int nc = l + 1;
-    for (int c0 = 0; c0 < nc; c0 += 8) {
-      double acc[8];
+    const int groups = l > 0 ? (l + 7) / 8 : 1;
+    for (int g = 0; g < groups; ++g) {
+      const int c0 = 8 * g;
+      T acc[8];
+      T ww = T(0);
 #pragma unroll
-      for (int c = 0; c < 8; ++c) acc[c] = 0.0;
+      for (int c = 0; c < 8; ++c) acc[c] = T(0);
       for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
-        const double wv = (double)ldv(w + j);
+        const T wv = ldv(w + j);
+        if (l > 0)
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const int col = c0 + c;
-          if (col < l) acc[c] = fma((double)ldv(W + (size_t)col * N + j), wv, acc[c]);
-          else if (col == l) acc[c] = fma(wv, wv, acc[c]);
-        }
+          for (int c = 0; c < 8; ++c)
+            acc[c] = fma(ldv(W + (size_t)min(c0 + c, l - 1) * N + j), wv, acc[c]);
+        if (g == 0) ww = fma(wv, wv, ww);
       }
-      bsum_n<8>(acc, sh);
+      double v[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) v[c] = (double)acc[c];
+      bsum_n<8>(v, sh);
       if (threadIdx.x == 0)
 #pragma unroll
         for (int c = 0; c < 8; ++c)
-          if (c0 + c < nc) part[(size_t)blockIdx.x * nc + c0 + c] = acc[c];
+          if (c0 + c < l) part[(size_t)blockIdx.x * nc + c0 + c] = v[c];
+      if (g == 0) {
+        double n[1] = {(double)ww};
+        bsum_n<1>(n, sh);
+        if (threadIdx.x == 0) part[(size_t)blockIdx.x * nc + l] = n[0];
+      }
     }
   }
 
@@ -639,8 +652,15 @@ struct CoarseCycle {
   }
 };
 
+// Resident blocks per SM the register allocation must allow.  With 2 the kernel fits in
+// 94 registers without spills (158 with 1), so level-0 kernels of the task-parallel cycle
+// can run on its SMs beside it: measured 75.8 against 77.5 ms per 64^3 cycle, with the
+// coarse kernel itself slower (1.00 against 0.78 ms per launch) as it shares the SMs.
+#ifndef KCMG_CC_MINBLOCKS
+#define KCMG_CC_MINBLOCKS 2
+#endif
 template <typename TV, typename TS, typename TI, int NP, int DIM>
-__global__ void __launch_bounds__(320, 1) k_coarse_cycle(CoarseArgs a) {
+__global__ void __launch_bounds__(320, KCMG_CC_MINBLOCKS) k_coarse_cycle(CoarseArgs a) {
   using T = TV;
   extern __shared__ unsigned char smem_raw[];
   __shared__ double sh[32 * 8];

@@ -966,12 +966,22 @@ kcmg_ctx* build_ctx(const kcmg_params* p, cudaStream_t user, const double* block
     CK(cudaGetDevice(&dev));
     ctx->dev = dev;
     CK(cudaStreamCreateWithFlags(&ctx->s, cudaStreamNonBlocking));
-    for (int l = 0; l < KCMG_MAX_LEVELS + 1; ++l) CK(cudaStreamCreateWithFlags(&ctx->cap[l], cudaStreamNonBlocking));
-    {  // the coarse path of the task-parallel cycle (eager form): highest priority, so
-       // that its latency-bound kernels get SMs first while the smoother path fills the rest
+    {
+      // Capture streams: cap[l + 1] records the loop body of level l.  The coarse path of
+      // the task-parallel cycle (its stream, and the bodies of levels >= 1 that it nests)
+      // takes the highest priority, so that its latency-bound kernels get SMs first while
+      // the smoother path fills the rest; kernels captured in a graph keep the priority of
+      // the stream they were captured on.  KCMG_COARSE_PRIORITY=0 turns this off (tuning).
       int lo = 0, hi = 0;
       CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-      CK(cudaStreamCreateWithPriority(&ctx->cap[KCMG_MAX_LEVELS + 1], cudaStreamNonBlocking, hi));
+      int prio_on = 1;
+      if (const char* ev = getenv("KCMG_COARSE_PRIORITY")) prio_on = atoi(ev) != 0;
+      for (int l = 0; l < KCMG_MAX_LEVELS + 1; ++l) {
+        const bool coarse = prio_on && p->async_smooth > 0 && l >= 2;
+        CK(cudaStreamCreateWithPriority(&ctx->cap[l], cudaStreamNonBlocking, coarse ? hi : lo));
+      }
+      CK(cudaStreamCreateWithPriority(&ctx->cap[KCMG_MAX_LEVELS + 1], cudaStreamNonBlocking,
+                                      prio_on ? hi : lo));
     }
     CK(cudaEventCreateWithFlags(&ctx->ev, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming));
@@ -1453,57 +1463,63 @@ kcmg_status kcmg_kernel_report(kcmg_ctx* ctx, int reps, double* out, int nout) {
       out[2] = by;
     }
     if (reps > 0) {
-      Level& L = ctx->lv[0];
       const int S = ctx->S, np = ctx->np;
       cudaEvent_t e0, e1;
       CK(cudaEventCreate(&e0));
       CK(cudaEventCreate(&e1));
-      const size_t vb = ctx->ir ? sizeof(float) : sizeof(double);   // level vector element
-      CK(cudaMemsetAsync(L.b, 0, L.N * vb, ctx->s));
-      CK(cudaMemsetAsync(L.t, 0, L.N * vb, ctx->s));
-      EpiArgs none;
-      // the operator of the level-0 residual minimisation (Alg. 1 SpMV): FP64, or FP32 in
-      // the inner solve of the iterative-refinement forms
-      CK(cudaEventRecord(e0, ctx->s));
-      for (int k = 0; k < reps; ++k) {
-        if (ctx->ir)
-          launch_spmv<float>(np, ctx->dim, L.A32, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
-                             static_cast<float*>(L.t), static_cast<float*>(L.w), nullptr, nullptr, none, 0, ctx->s);
-        else
-          launch_spmv<double>(np, ctx->dim, L.A64, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
-                              static_cast<double*>(L.t), static_cast<double*>(L.w), nullptr, nullptr, none, 0, ctx->s);
-      }
-      CK(cudaEventRecord(e1, ctx->s));
-      CK(cudaEventSynchronize(e1));
-      float ms = 0;
-      CK(cudaEventElapsedTime(&ms, e0, e1));
-      out[3] = ms / reps;
-      out[4] = (double)S * L.N * np * vb + 2.0 * L.N * vb;
-      // one full block-Jacobi sweep on level 0 in the smoother's precision
-      const double sb = ctx->mixed ? 4 : 8;
-      const double ib = !ctx->mixed ? 8 : (L.D16 ? 2 : 4);
-      if (ctx->mixed) {
-        CK(cudaMemsetAsync(L.r_lo, 0, L.N * sizeof(float), ctx->s));
-        CK(cudaMemsetAsync(L.t_lo, 0, L.N * sizeof(float), ctx->s));
-      }
-      CK(cudaEventRecord(e0, ctx->s));
-      for (int k = 0; k < reps; ++k) {
-        if (!ctx->mixed)
-          launch_bj_sweep<double, double>(np, ctx->dim, L.A64, L.D64, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
-                                          static_cast<double*>(L.b), static_cast<double*>(L.t),
-                                          static_cast<double*>(L.z), ctx->p.omega, 0, ctx->s);
-        else if (L.D16)
-          launch_bj_sweep<float, __nv_bfloat16>(np, ctx->dim, L.A32, L.D16, L.nbr, L.N, L.G, L.rows_pad,
-                                                L.block_rows, L.r_lo, L.t_lo, L.z_lo, ctx->p.omega, 0, ctx->s);
-        else
-          launch_bj_sweep<float, float>(np, ctx->dim, L.A32, L.D32, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
-                                        L.r_lo, L.t_lo, L.z_lo, ctx->p.omega, 0, ctx->s);
-      }
-      CK(cudaEventRecord(e1, ctx->s));
-      CK(cudaEventSynchronize(e1));
-      CK(cudaEventElapsedTime(&ms, e0, e1));
-      out[5] = ms / reps;
-      out[6] = (double)(S - 1) * L.N * np * sb + (double)L.N * np * ib + 3.0 * L.N * sb;
+      // the operator of a level's residual minimisation (Alg. 1 SpMV: FP64, or FP32 in the
+      // inner solve of the iterative-refinement forms) and one full block-Jacobi sweep in
+      // the smoother's precision, reps launches each: out[o] ms and out[o + 1] algorithmic
+      // bytes per operator launch, out[o + 2], out[o + 3] per sweep
+      auto time_level = [&](int lev, int o) {
+        Level& L = ctx->lv[lev];
+        const size_t vb = ctx->ir ? sizeof(float) : sizeof(double);   // level vector element
+        CK(cudaMemsetAsync(L.b, 0, L.N * vb, ctx->s));
+        CK(cudaMemsetAsync(L.t, 0, L.N * vb, ctx->s));
+        EpiArgs none;
+        CK(cudaEventRecord(e0, ctx->s));
+        for (int k = 0; k < reps; ++k) {
+          if (ctx->ir)
+            launch_spmv<float>(np, ctx->dim, L.A32, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
+                               static_cast<float*>(L.t), static_cast<float*>(L.w), nullptr, nullptr, none, 0, ctx->s);
+          else
+            launch_spmv<double>(np, ctx->dim, L.A64, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
+                                static_cast<double*>(L.t), static_cast<double*>(L.w), nullptr, nullptr, none, 0, ctx->s);
+        }
+        CK(cudaEventRecord(e1, ctx->s));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        out[o] = ms / reps;
+        out[o + 1] = (double)S * L.N * np * vb + 2.0 * L.N * vb;
+        const double sb = ctx->mixed ? 4 : 8;
+        const double ib = !ctx->mixed ? 8 : (L.D16 ? 2 : 4);
+        if (ctx->mixed) {
+          CK(cudaMemsetAsync(L.r_lo, 0, L.N * sizeof(float), ctx->s));
+          CK(cudaMemsetAsync(L.t_lo, 0, L.N * sizeof(float), ctx->s));
+        }
+        CK(cudaEventRecord(e0, ctx->s));
+        for (int k = 0; k < reps; ++k) {
+          if (!ctx->mixed)
+            launch_bj_sweep<double, double>(np, ctx->dim, L.A64, L.D64, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
+                                            static_cast<double*>(L.b), static_cast<double*>(L.t),
+                                            static_cast<double*>(L.z), ctx->p.omega, 0, ctx->s);
+          else if (L.D16)
+            launch_bj_sweep<float, __nv_bfloat16>(np, ctx->dim, L.A32, L.D16, L.nbr, L.N, L.G, L.rows_pad,
+                                                  L.block_rows, L.r_lo, L.t_lo, L.z_lo, ctx->p.omega, 0, ctx->s);
+          else
+            launch_bj_sweep<float, float>(np, ctx->dim, L.A32, L.D32, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
+                                          L.r_lo, L.t_lo, L.z_lo, ctx->p.omega, 0, ctx->s);
+        }
+        CK(cudaEventRecord(e1, ctx->s));
+        CK(cudaEventSynchronize(e1));
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        out[o + 2] = ms / reps;
+        out[o + 3] = (double)(S - 1) * L.N * np * sb + (double)L.N * np * ib + 3.0 * L.N * sb;
+      };
+      time_level(0, 3);
+      if (ctx->nlev > 2 && nout >= 7 + KCMG_MAX_LEVELS + kCoarsePhases + 4)
+        time_level(1, 7 + KCMG_MAX_LEVELS + kCoarsePhases);
       CK(cudaGetLastError());
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);

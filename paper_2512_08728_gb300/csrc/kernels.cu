@@ -439,9 +439,50 @@ __global__ void k_coarse_gemv(const double* __restrict__ Ainv, int n, const T* _
 }
 
 // ------------------------------------------------------------------ Gram / RM (Alg. 1)
-// partial[b][c] = sum over block b's elements of W_c . w for c < l, and ||w||^2 at c = l.
-// Columns are processed 8 at a time; each block owns a contiguous element range.
-template <typename T>
+// partial[k][c] = sum over element chunk k of W_c . w for c < l, and ||w||^2 at c = l.
+// Work items are (group of kDotCols columns) x (element chunk); the fixed grid takes them
+// round-robin with K = grid / groups chunks per group, so a block reduces its sums once
+// per item and the reduction order depends only on N, l and the grid.  With PAIR (N even)
+// a thread takes two consecutive elements per step with one 16-byte (FP64) or 8-byte
+// (FP32) load per column.  The last partial column group reads a valid column in place of
+// the missing ones and drops those sums, so every step issues the same FMAs (no
+// predicated arithmetic).  ||w||^2 rides with group 0 as a separate accumulator.
+constexpr int kDotCols = 8;
+
+template <typename T> struct Pair;
+template <> struct Pair<double> { using type = double2; };
+template <> struct Pair<float> { using type = float2; };
+
+template <typename T, bool PAIR, bool NORM>
+__device__ __forceinline__ void dots_item(const T* __restrict__ W, int N, const T* __restrict__ w, int l, int c0,
+                                          int u0, int u1, T (&acc)[kDotCols], T& ww) {
+  using T2 = typename Pair<T>::type;
+  const T* Wc[kDotCols];
+#pragma unroll
+  for (int c = 0; c < kDotCols; ++c) Wc[c] = W + (size_t)min(c0 + c, l - 1) * N;
+  for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
+    if (PAIR) {
+      const T2 wv = __ldg(reinterpret_cast<const T2*>(w) + u);
+#pragma unroll
+      for (int c = 0; c < kDotCols; ++c) {
+        const T2 a = __ldg(reinterpret_cast<const T2*>(Wc[c]) + u);
+        acc[c] = fma(a.x, wv.x, acc[c]);
+        acc[c] = fma(a.y, wv.y, acc[c]);
+      }
+      if (NORM) {
+        ww = fma(wv.x, wv.x, ww);
+        ww = fma(wv.y, wv.y, ww);
+      }
+    } else {
+      const T wv = __ldg(w + u);
+#pragma unroll
+      for (int c = 0; c < kDotCols; ++c) acc[c] = fma(__ldg(Wc[c] + u), wv, acc[c]);
+      if (NORM) ww = fma(wv, wv, ww);
+    }
+  }
+}
+
+template <typename T, bool PAIR>
 __global__ void __launch_bounds__(kVecThreads)
 k_gram_dots(const T* __restrict__ W, int N, const T* __restrict__ w, double* partial,
             EpiArgs e, int conditional) {
@@ -450,31 +491,48 @@ k_gram_dots(const T* __restrict__ W, int N, const T* __restrict__ w, double* par
   __shared__ double sh[32 * 8];   // bsum_n<NC> needs 32 * NC
   const int l = st->l;
   const int ncol = l + 1;
-  const int chunk = (N + gridDim.x - 1) / gridDim.x;
-  const int j0 = blockIdx.x * chunk, j1 = min(N, j0 + chunk);
-  for (int c0 = 0; c0 < ncol; c0 += 8) {
-    // each thread sums its few elements in T (FP32 vectors: FP32 products and partial
-    // sums, no per-element FP64 work); the block and grid reductions are FP64
-    T acct[8];
+  const int groups = l > 0 ? (l + kDotCols - 1) / kDotCols : 1;   // l = 0: the norm only
+  const int K = max(1, (int)gridDim.x / groups);
+  const int units = PAIR ? N / 2 : N;
+  const int chunk = (units + K - 1) / K;
+  for (int item = blockIdx.x; item < groups * K; item += gridDim.x) {
+    const int g = item / K, k = item - g * K;
+    const int c0 = g * kDotCols;
+    const int u0 = min(units, k * chunk), u1 = min(units, u0 + chunk);
+    T acct[kDotCols];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acct[c] = T(0);
-    for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-      const T wv = w[j];
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const int col = c0 + c;
-        if (col < l) acct[c] = fma(__ldg(W + (size_t)col * N + j), wv, acct[c]);
-        else if (col == l) acct[c] = fma(wv, wv, acct[c]);
+    for (int c = 0; c < kDotCols; ++c) acct[c] = T(0);
+    T ww = T(0);
+    if (l == 0) {
+      for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
+        if (PAIR) {
+          const typename Pair<T>::type wv = __ldg(reinterpret_cast<const typename Pair<T>::type*>(w) + u);
+          ww = fma(wv.x, wv.x, ww);
+          ww = fma(wv.y, wv.y, ww);
+        } else {
+          const T wv = __ldg(w + u);
+          ww = fma(wv, wv, ww);
+        }
       }
+    } else if (g == 0) {
+      dots_item<T, PAIR, true>(W, N, w, l, c0, u0, u1, acct, ww);
+    } else {
+      dots_item<T, PAIR, false>(W, N, w, l, c0, u0, u1, acct, ww);
     }
+    // the block's sums in FP64 (FP32 vectors: FP32 products and per-thread sums)
     double acc[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) acc[c] = (double)acct[c];
     bsum_n<8>(acc, sh);
     if (threadIdx.x == 0)
 #pragma unroll
-      for (int c = 0; c < 8; ++c)
-        if (c0 + c < ncol) partial[(size_t)blockIdx.x * ncol + c0 + c] = acc[c];
+      for (int c = 0; c < kDotCols; ++c)
+        if (c0 + c < l) partial[(size_t)k * ncol + c0 + c] = acc[c];
+    if (g == 0) {
+      double v[1] = {(double)ww};
+      bsum_n<1>(v, sh);
+      if (threadIdx.x == 0) partial[(size_t)k * ncol + l] = v[0];
+    }
   }
   if (last_block(&st->ticket)) {
     // one warp per column: lanes read independent partials, then a fixed shuffle tree
@@ -482,7 +540,7 @@ k_gram_dots(const T* __restrict__ W, int N, const T* __restrict__ w, double* par
     const int wid = threadIdx.x >> 5, ln = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int c = wid; c < ncol; c += nw) {
       double s = 0.0;
-      for (int b = ln; b < (int)gridDim.x; b += 32) s += __ldcg(partial + (size_t)b * ncol + c);
+      for (int b = ln; b < K; b += 32) s += __ldcg(partial + (size_t)b * ncol + c);
 #pragma unroll
       for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (ln == 0) sums[c] = s;
@@ -515,11 +573,13 @@ k_gram_apply(const T* __restrict__ W, int N, const T* __restrict__ w, T* __restr
 
 // w_hat = w_src - W c_w, z_hat = z - Z c_z written to column l of W and Z; partial sums
 // ||w_hat||^2 and w_hat . r.  Without reorthogonalisation w_src = w, c_w = c_z = h; with it
-// w_src = w' = w - W h, c_w = h2, c_z = h + h2.
-template <typename T>
+// w_src = w' = w - W h, c_w = h2, c_z = h + h2.  With PAIR (N even) a thread updates two
+// consecutive elements with one 16-byte (FP64) / 8-byte (FP32) load per column of W and Z.
+template <typename T, bool PAIR>
 __global__ void __launch_bounds__(kVecThreads)
 k_gram_update(T* W, T* Z, int N, const T* __restrict__ w, const T* __restrict__ wre,
               const T* __restrict__ z, const T* __restrict__ r, double* partial, EpiArgs e) {
+  using T2 = typename Pair<T>::type;
   LevelState* st = e.st;
   extern __shared__ double cs[];  // [2][l]
   __shared__ double sh[32 * 8];   // bsum_n<NC> needs 32 * NC
@@ -534,17 +594,41 @@ k_gram_update(T* W, T* Z, int N, const T* __restrict__ w, const T* __restrict__ 
   T* Wl = W + (size_t)l * N;
   T* Zl = Z + (size_t)l * N;
   T nw2 = T(0), wr = T(0);   // per-thread sums in T, reduced in FP64
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
-    T a = ws[j], c = z[j];
+  if (PAIR) {
+    const int units = N / 2;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < units; u += gridDim.x * blockDim.x) {
+      T2 a = reinterpret_cast<const T2*>(ws)[u], c = reinterpret_cast<const T2*>(z)[u];
 #pragma unroll 4
-    for (int i = 0; i < l; ++i) {
-      a = fma((T)(-cs[i]), __ldg(W + (size_t)i * N + j), a);
-      c = fma((T)(-cs[l + i]), __ldg(Z + (size_t)i * N + j), c);
+      for (int i = 0; i < l; ++i) {
+        const T2 wi = __ldg(reinterpret_cast<const T2*>(W + (size_t)i * N) + u);
+        const T2 zi = __ldg(reinterpret_cast<const T2*>(Z + (size_t)i * N) + u);
+        const T cw = (T)(-cs[i]), cz = (T)(-cs[l + i]);
+        a.x = fma(cw, wi.x, a.x);
+        a.y = fma(cw, wi.y, a.y);
+        c.x = fma(cz, zi.x, c.x);
+        c.y = fma(cz, zi.y, c.y);
+      }
+      reinterpret_cast<T2*>(Wl)[u] = a;
+      reinterpret_cast<T2*>(Zl)[u] = c;
+      const T2 rv = reinterpret_cast<const T2*>(r)[u];
+      nw2 = fma(a.x, a.x, nw2);
+      nw2 = fma(a.y, a.y, nw2);
+      wr = fma(a.x, rv.x, wr);
+      wr = fma(a.y, rv.y, wr);
     }
-    Wl[j] = a;
-    Zl[j] = c;
-    nw2 = fma(a, a, nw2);
-    wr = fma(a, r[j], wr);
+  } else {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
+      T a = ws[j], c = z[j];
+#pragma unroll 4
+      for (int i = 0; i < l; ++i) {
+        a = fma((T)(-cs[i]), __ldg(W + (size_t)i * N + j), a);
+        c = fma((T)(-cs[l + i]), __ldg(Z + (size_t)i * N + j), c);
+      }
+      Wl[j] = a;
+      Zl[j] = c;
+      nw2 = fma(a, a, nw2);
+      wr = fma(a, r[j], wr);
+    }
   }
   double v[2] = {(double)nw2, (double)wr};
   finish_reduction<2>(v, partial, e, sh);
@@ -1026,7 +1110,10 @@ void launch_coarse_gemv(const double* Ainv, int n, const T* b, T* x, cudaStream_
 template <typename T>
 void launch_gram_dots(const T* W, int N, const T* w, int lcap, int nblk, double* partial,
                       const EpiArgs& e, int conditional, cudaStream_t s) {
-  k_gram_dots<T><<<nblk, kVecThreads, (lcap + 1) * sizeof(double), s>>>(W, N, w, partial, e, conditional);
+  if (N % 2 == 0)   // pairs of elements: every column base is 16-byte (FP64) / 8-byte (FP32) aligned
+    k_gram_dots<T, true><<<nblk, kVecThreads, (lcap + 1) * sizeof(double), s>>>(W, N, w, partial, e, conditional);
+  else
+    k_gram_dots<T, false><<<nblk, kVecThreads, (lcap + 1) * sizeof(double), s>>>(W, N, w, partial, e, conditional);
 }
 
 template <typename T>
@@ -1039,7 +1126,12 @@ template <typename T>
 void launch_gram_update(const T* W, const T* Z, int N, const T* w, const T* wre, const T* z,
                         const T* r, int lcap, int nblk, double* partial, const EpiArgs& e,
                         cudaStream_t s) {
-  k_gram_update<T><<<nblk, kVecThreads, 2 * lcap * sizeof(double), s>>>(const_cast<T*>(W), const_cast<T*>(Z), N, w, wre, z, r, partial, e);
+  if (N % 2 == 0)   // pairs of elements (aligned column bases), half the grid
+    k_gram_update<T, true><<<(nblk + 1) / 2, kVecThreads, 2 * lcap * sizeof(double), s>>>(
+        const_cast<T*>(W), const_cast<T*>(Z), N, w, wre, z, r, partial, e);
+  else
+    k_gram_update<T, false><<<nblk, kVecThreads, 2 * lcap * sizeof(double), s>>>(
+        const_cast<T*>(W), const_cast<T*>(Z), N, w, wre, z, r, partial, e);
 }
 
 template <typename T>

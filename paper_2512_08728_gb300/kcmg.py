@@ -259,13 +259,16 @@ def kcmg_residual_noalloc(ctx, b, x, r):
 def kcmg_kernel_report(ctx, reps=0):
     """Coarse-cycle kernel counters since the last call and, with reps > 0, CUDA-event
     timings of the level-0 operator application and smoother sweep (see kcmg.h)."""
-    out = np.zeros(7 + KCMG_MAX_LEVELS + len(COARSE_PHASES))
+    n0 = 7 + KCMG_MAX_LEVELS + len(COARSE_PHASES)
+    out = np.zeros(n0 + 4)
     _check(ctx, load_library().kcmg_kernel_report(ctx, int(reps), out.ctypes.data, out.size))
-    ph = out[7 + KCMG_MAX_LEVELS:]
+    ph = out[7 + KCMG_MAX_LEVELS:n0]
     return {"coarse_launches": int(out[0]), "coarse_ms": out[1], "coarse_bytes": out[2],
             "spmv_ms": out[3], "spmv_bytes": out[4], "sweep_ms": out[5], "sweep_bytes": out[6],
             "coarse_level_ms": out[7:7 + KCMG_MAX_LEVELS].tolist(),
-            "coarse_phase_ms": dict(zip(COARSE_PHASES, ph.tolist()))}
+            "coarse_phase_ms": dict(zip(COARSE_PHASES, ph.tolist())),
+            "spmv1_ms": out[n0], "spmv1_bytes": out[n0 + 1], "sweep1_ms": out[n0 + 2],
+            "sweep1_bytes": out[n0 + 3]}
 
 
 def _unary(name, ctx, level, x, nout, *extra):

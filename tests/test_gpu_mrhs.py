@@ -20,6 +20,11 @@ from workloads import make_problem, workload
 
 pytestmark = pytest.mark.gpu
 
+# batched solves whose columns the oracle re-evaluates against 1e-10 stop at 9e-11: the
+# GPU confirms each column on a compensated FP64 residual, the oracle evaluates it with
+# plain FP64 sums, and the two readings differ by rounding
+RTOL_GPU = 9e-11
+
 
 @pytest.fixture(scope="module", autouse=True)
 def _built():
@@ -99,7 +104,7 @@ def _check_columns(pr, X, info, rtol=1e-10, tol_err=1e-8):
 def test_batched_solve_matches_oracle_per_column(name, nrhs, precision):
     pr = _problem(name, nrhs=nrhs)
     s = pkg.KCycleSolver(pr, precision=precision)
-    X, info = s.solve(pr.b, rtol=1e-10, maxiter=2000)
+    X, info = s.solve(pr.b, rtol=RTOL_GPU, maxiter=2000)
     s.close()
     assert info["status"] == 0, info
     assert X.shape == pr.b.shape
@@ -109,14 +114,14 @@ def test_batched_solve_matches_oracle_per_column(name, nrhs, precision):
 def test_batched_columns_equal_single_solves_and_device_inputs():
     pr = _problem("sipg3d_p2_8cube", seed=4, nrhs=6)
     s = pkg.KCycleSolver(pr, precision="mixed")
-    Xh, info_h = s.solve(pr.b, rtol=1e-10, maxiter=2000)
+    Xh, info_h = s.solve(pr.b, rtol=RTOL_GPU, maxiter=2000)
     Bd = torch.from_numpy(pr.b).cuda()
-    Xd, info_d = s.solve(Bd, rtol=1e-10, maxiter=2000)
+    Xd, info_d = s.solve(Bd, rtol=RTOL_GPU, maxiter=2000)
     assert info_h["status"] == 0 and info_d["status"] == 0
     # host and device inputs run the same kernels on the same data
     assert np.array_equal(Xh, Xd.cpu().numpy())
     for j in range(pr.b.shape[1]):
-        xj, ij = s.solve(np.ascontiguousarray(pr.b[:, j]), rtol=1e-10, maxiter=2000)
+        xj, ij = s.solve(np.ascontiguousarray(pr.b[:, j]), rtol=RTOL_GPU, maxiter=2000)
         assert ij["status"] == 0
         assert np.linalg.norm(Xh[:, j] - xj) <= 1e-8 * np.linalg.norm(xj)
     t = s.mrhs_tuning()
@@ -153,8 +158,8 @@ def test_batched_masks_and_degenerate_columns():
 def test_batched_adjoint_equals_forward_for_symmetric_operator():
     pr = _problem("sipg3d_p1_8x4x4", seed=7, nrhs=4)
     s = pkg.KCycleSolver(pr, precision="fp64")
-    X, i1 = s.solve(pr.b, rtol=1e-10, maxiter=2000)
-    L, i2 = s.solve(pr.b, rtol=1e-10, maxiter=2000, adjoint=True)
+    X, i1 = s.solve(pr.b, rtol=RTOL_GPU, maxiter=2000)
+    L, i2 = s.solve(pr.b, rtol=RTOL_GPU, maxiter=2000, adjoint=True)
     s.close()
     assert i1["status"] == 0 and i2["status"] == 0
     assert np.linalg.norm(X - L) <= 1e-9 * np.linalg.norm(X)
@@ -169,7 +174,7 @@ def test_batched_task_parallel_cycle_matches_oracle(name, nrhs, m, precision):
     AsyncMG solve of that column."""
     pr = _problem(name, nrhs=nrhs)
     s = pkg.KCycleSolver(pr, precision=precision, async_smooth=m)
-    X, info = s.solve(pr.b, rtol=1e-10, maxiter=2000)
+    X, info = s.solve(pr.b, rtol=RTOL_GPU, maxiter=2000)
     s.close()
     assert info["status"] == 0, info
     orc = OracleSolver.from_problem(pr, async_smooth=m)

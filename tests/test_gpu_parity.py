@@ -15,6 +15,12 @@ from workloads import dense_matrix, make_problem, workload
 
 pytestmark = pytest.mark.gpu
 
+# GPU solves whose true residual the oracle re-evaluates against 1e-10 stop at 9e-11.  The
+# GPU tests convergence on a compensated FP64 residual; the oracle evaluates the same
+# residual with plain FP64 sums.  The two readings differ by rounding (measured 1.3e-13
+# relative), so a solve stopped exactly at 1e-10 can read just above it in the oracle.
+RTOL_GPU = 9e-11
+
 SMALL = ["sipg2d_p1_16x16", "sipg3d_p1_8x4x4", "sipg2d_p2_32x16", "sipg3d_p2_8cube",
          "sipg3d_p3_8cube_zstretch"]
 
@@ -139,7 +145,7 @@ def test_fp64_solve_matches_oracle(name, use_graph, persistent):
     x_or, info_or = OracleSolver.from_problem(pr).solve(pr.b, rtol=1e-10, maxiter=400)
     assert info_or["status"] == 0
     s = pkg.KCycleSolver(pr, precision="fp64", use_graph=use_graph, coarse_persistent=persistent)
-    x, info = s.solve(pr.b, rtol=1e-10, maxiter=400)
+    x, info = s.solve(pr.b, rtol=RTOL_GPU, maxiter=400)
     s.close()
     assert info["status"] == 0, info
     _check_solution(pr, x, info, x_or)
@@ -155,7 +161,7 @@ def test_mixed_precision_solve_matches_fp64_oracle(name, precision, persistent):
     pr = _problem(name)
     x_or, _ = OracleSolver.from_problem(pr).solve(pr.b, rtol=1e-10, maxiter=400)
     s = pkg.KCycleSolver(pr, precision=precision, use_graph=True, coarse_persistent=persistent)
-    x, info = s.solve(pr.b, rtol=1e-10, maxiter=2000)
+    x, info = s.solve(pr.b, rtol=RTOL_GPU, maxiter=2000)
     s.close()
     assert info["status"] == 0, info
     _check_solution(pr, x, info, x_or)
@@ -228,7 +234,7 @@ def test_persistent_and_per_kernel_coarse_cycles_agree():
     res = []
     for persistent in (False, True):
         s = pkg.KCycleSolver(pr, precision="fp64", coarse_persistent=persistent)
-        x, info = s.solve(pr.b, rtol=1e-10, maxiter=400)
+        x, info = s.solve(pr.b, rtol=RTOL_GPU, maxiter=400)
         s.close()
         assert info["status"] == 0
         res.append((x, info))
@@ -281,7 +287,7 @@ def test_task_parallel_cycle_matches_oracle(name, m, use_graph, persistent):
     assert info_or["status"] == 0
     s = pkg.KCycleSolver(pr, precision="fp64", use_graph=use_graph, coarse_persistent=persistent,
                          async_smooth=m)
-    x, info = s.solve(pr.b, rtol=1e-10, maxiter=2000)
+    x, info = s.solve(pr.b, rtol=RTOL_GPU, maxiter=2000)
     s.close()
     assert info["status"] == 0, info
     _check_solution(pr, x, info, x_or)
@@ -310,7 +316,7 @@ def test_task_parallel_mixed_precision(precision):
     pr = _problem("sipg3d_p2_8cube")
     x_or, _ = OracleSolver.from_problem(pr, async_smooth=2).solve(pr.b, rtol=1e-10, maxiter=2000)
     s = pkg.KCycleSolver(pr, precision=precision, use_graph=True, async_smooth=2)
-    x, info = s.solve(pr.b, rtol=1e-10, maxiter=2000)
+    x, info = s.solve(pr.b, rtol=RTOL_GPU, maxiter=2000)
     s.close()
     assert info["status"] == 0, info
     _check_solution(pr, x, info, x_or)
@@ -328,7 +334,7 @@ def test_task_parallel_graph_and_eager_are_bitwise_identical():
 
 
 # ------------------------------------------------------------------ the benchmark's level layout
-def _layout_solve(pr, m, rows_max, monkeypatch, lmax=200, rtol=1e-10):
+def _layout_solve(pr, m, rows_max, monkeypatch, lmax=200, rtol=RTOL_GPU):
     """Solve with the persistent coarse kernel taking the levels from the first one with at
     most rows_max rows (set through KCMG_PERSISTENT_ROWS at setup); the levels above it run
     one kernel per step under nested conditional graph nodes."""
@@ -391,7 +397,7 @@ def test_iterative_refinement_solve_matches_fp64_oracle(name, precision, m, pers
     x_or, _ = OracleSolver.from_problem(pr).solve(pr.b, rtol=1e-10, maxiter=400)
     s = pkg.KCycleSolver(pr, precision=precision, use_graph=True, coarse_persistent=persistent,
                          async_smooth=m)
-    x, info = s.solve(pr.b, rtol=1e-10, maxiter=4000)
+    x, info = s.solve(pr.b, rtol=RTOL_GPU, maxiter=4000)
     s.close()
     assert info["status"] == 0, info
     _check_solution(pr, x, info, x_or)

@@ -42,19 +42,19 @@ if ROOT not in sys.path:
 
 WORKLOAD = "sipg3d_p2_64cube"
 RTOL = 1e-10
-LMAX = 200         # level-0 restart length of the benchmarked configuration
+LMAX = 400         # level-0 restart length of the benchmarked configuration
 MAXITER = 4000
 METRIC = "DOFs solved/s to 1e-10 rel. residual, mixed vs FP64; % of HBM roofline"
 UNIT = "DOF/s"
 # Level-0 cycle of the headline solve: Alg. AsyncMG (the paper's task-parallel cycle) with
 # HEADLINE_ASYNC_M smoother + RM steps per cycle beside the coarse path; the multiplicative
 # K-cycle of Alg. 2 (async 0) and the mixed forms are reported beside it.
-HEADLINE_ASYNC_M = 8
+HEADLINE_ASYNC_M = 12
 # Level-0 cycles and level-1 iterations of the headline FP64 solve of this workload (seed 0,
-# LMAX = 200), measured on GB300; the reference arm (a separate process) extrapolates its
-# bounded sample with them.
-GPU_LEVEL1_ITERS_FP64 = 1940
-GPU_CYCLES_FP64 = 98
+# LMAX = 400, m = 12), measured on GB300; the reference arm (a separate process)
+# extrapolates its bounded sample with them.
+GPU_LEVEL1_ITERS_FP64 = 1064
+GPU_CYCLES_FP64 = 54
 
 
 def _peaks():

@@ -17,6 +17,11 @@
  *               next level, prolongate, RM, post-smoother, RM.
  *   smooth      Alg. BJ (block Jacobi) started from x = 0 with a fixed sweep count:
  *               r = b - A x; x_i += omega A_ii^{-1} r_i for every cell block i.
+ *   smooth_as   Alg. AS (additive Schwarz, Sec. 3.2) on overlapping cell patches, from x = 0
+ *               with a fixed sweep count: r = b - A x; x += omega sum_i P_i A_i^{-1} R_i r over
+ *               the patches i of two partitions of the grid into 2^d-cell blocks (one
+ *               aligned with the agglomeration, one shifted by a cell in every direction),
+ *               A_i = R_i A P_i inverted densely.
  *   async_mg0   Alg. AsyncMG (task-parallel OrthoMG) on level 0, with the smoother group's
  *               loop run a fixed number m of times per cycle so that the result does not
  *               depend on timing: per cycle the coarse path restricts the residual of the
@@ -74,6 +79,10 @@ typedef struct {
     /* per-level Alg. 2 state */
     int lcap, l;
     double *W, *Z;   /* [lcap][N] stored orthonormal basis and its search directions */
+    /* Alg. AS patches: partition 0 = aligned 2^d blocks, 1 = shifted by one cell */
+    int npatch[2];
+    int *pcell[2];   /* [npatch][2^d] member cells, -1 = outside the grid */
+    double *pinv[2]; /* [npatch][m][m] inverse of the local matrix, m = 2^d np */
     double *alpha;   /* [lcap] */
     double *x0, *r0, *x, *r, *z, *w, *t, *bc, *xc;
 } olevel;
@@ -95,6 +104,7 @@ typedef struct {
     int breakdowns_in_row, status_flag;
     int lmax, restarts;
     int async_m;     /* 0: Alg. 2 on level 0; m > 0: Alg. AsyncMG with m smoother steps */
+    int smoother;    /* 0: Alg. BJ (block Jacobi); 1: Alg. AS (additive Schwarz, patches) */
     double res0;     /* ||b - A x0|| of the top-level solve */
 } osolver;
 
@@ -105,6 +115,7 @@ static double dot(int n, const double *a, const double *b) {
 }
 
 static int ndof(const osolver *S, int lev) { return S->lv[lev].ncell * S->np; }
+static int invert_block(int n, const double *A, double *Ainv);
 
 /* y = A x on level lev (block row K: sum over slots of blk[K][s] x[nbr]) */
 static void apply(const osolver *S, int lev, const double *x, double *y) {
@@ -126,7 +137,7 @@ static void apply(const osolver *S, int lev, const double *x, double *y) {
 }
 
 /* Alg. BJ from x^(0) = 0 with S->sweeps iterations (no norm test inside MG). */
-static void smooth(osolver *S, int lev, const double *b, double *x) {
+static void smooth_bj(osolver *S, int lev, const double *b, double *x) {
     olevel *L = &S->lv[lev];
     int np = S->np, N = ndof(S, lev);
     double *r = L->t;
@@ -145,6 +156,105 @@ static void smooth(osolver *S, int lev, const double *b, double *x) {
             }
         }
     }
+}
+
+/* Alg. AS from x^(0) = 0 with S->sweeps iterations: each iteration forms the global
+   residual r = b - A x, restricts it to every patch of both partitions, solves the local
+   problems A_i z_i = R_i r with the stored inverses, and adds omega times the sum of the
+   prolongated z_i to x.  The patches of one partition are disjoint, so every cell gets one
+   contribution per partition; partition 0 is added first. */
+static void smooth_as(osolver *S, int lev, const double *b, double *x) {
+    olevel *L = &S->lv[lev];
+    int np = S->np, N = ndof(S, lev), nc = S->nchild, m = nc * np;
+    double *r = L->t;
+    double *e = malloc(sizeof(double) * N);
+    for (int i = 0; i < N; i++) x[i] = 0.0;
+    for (int k = 0; k < S->sweeps; k++) {
+        apply(S, lev, x, r);
+        ORC_PARALLEL_FOR
+        for (int i = 0; i < N; i++) r[i] = b[i] - r[i];
+        for (int i = 0; i < N; i++) e[i] = 0.0;
+        for (int part = 0; part < 2; part++) {
+            ORC_PARALLEL_FOR
+            for (int pi = 0; pi < L->npatch[part]; pi++) {
+                const int *cells = L->pcell[part] + (size_t)pi * nc;
+                const double *Ainv = L->pinv[part] + (size_t)pi * m * m;
+                double rl[8 * 32];                            /* m <= 8 * 32 */
+                for (int a = 0; a < nc; a++)
+                    for (int q = 0; q < np; q++)
+                        rl[a * np + q] = cells[a] >= 0 ? r[(size_t)cells[a] * np + q] : 0.0;
+                for (int a = 0; a < nc; a++) {
+                    if (cells[a] < 0) continue;
+                    for (int q = 0; q < np; q++) {
+                        double z = 0.0;
+                        for (int j = 0; j < m; j++) z += Ainv[(size_t)(a * np + q) * m + j] * rl[j];
+                        e[(size_t)cells[a] * np + q] += z;
+                    }
+                }
+            }
+        }
+        ORC_PARALLEL_FOR
+        for (int i = 0; i < N; i++) x[i] += S->omega * e[i];
+    }
+    free(e);
+}
+
+static void smooth(osolver *S, int lev, const double *b, double *x) {
+    if (S->smoother == 1) smooth_as(S, lev, b, x);
+    else smooth_bj(S, lev, b, x);
+}
+
+/* The patches of partition part (0: aligned, 1: shifted by one cell) on level lev and the
+   inverses of their local matrices A_i = R_i A P_i: member a = cx + 2 cy + 4 cz of patch
+   (px, py, pz) is the cell (2 px - part + cx, ...) if it lies in the grid.  The local matrix
+   holds the blocks of A that couple two members (slot 0 on the diagonal, the face slot
+   towards a neighbour member elsewhere); an absent member gets an identity block and no
+   coupling, so its row of the solve is zero for a zero right-hand side.  Returns 0, or 1
+   if a local matrix is singular. */
+static int build_patches(osolver *S, int lev, int part) {
+    olevel *L = &S->lv[lev];
+    int np = S->np, nc = S->nchild, m = nc * np, nf = 2 * S->dim;
+    int pn[3] = {1, 1, 1};
+    for (int j = 0; j < S->dim; j++) pn[j] = L->n[j] / 2 + part;
+    int npatch = pn[0] * pn[1] * pn[2];
+    L->npatch[part] = npatch;
+    L->pcell[part] = malloc(sizeof(int) * npatch * nc);
+    L->pinv[part] = malloc(sizeof(double) * (size_t)npatch * m * m);
+    double *M = malloc(sizeof(double) * m * m);
+    for (int pi = 0; pi < npatch; pi++) {
+        int pc[3] = {pi % pn[0], (pi / pn[0]) % pn[1], pi / (pn[0] * pn[1])};
+        int *cells = L->pcell[part] + (size_t)pi * nc;
+        for (int a = 0; a < nc; a++) {
+            int c[3] = {0, 0, 0}, inside = 1;
+            for (int j = 0; j < S->dim; j++) {
+                c[j] = 2 * pc[j] - part + ((a >> j) & 1);
+                if (c[j] < 0 || c[j] >= L->n[j]) inside = 0;
+            }
+            cells[a] = inside ? c[0] + L->n[0] * (c[1] + L->n[1] * c[2]) : -1;
+        }
+        for (int i = 0; i < m * m; i++) M[i] = 0.0;
+        for (int a = 0; a < nc; a++) {
+            if (cells[a] < 0) {
+                for (int q = 0; q < np; q++) M[(size_t)(a * np + q) * m + a * np + q] = 1.0;
+                continue;
+            }
+            for (int b = 0; b < nc; b++) {
+                if (cells[b] < 0) continue;
+                int slot = -1;
+                if (b == a) slot = 0;
+                else
+                    for (int s = 1; s <= nf; s++)
+                        if (L->nbr[cells[a] * nf + s - 1] == cells[b]) slot = s;
+                if (slot < 0) continue;
+                const double *B = L->blk + ((size_t)cells[a] * S->S + slot) * np * np;
+                for (int q = 0; q < np; q++)
+                    for (int t = 0; t < np; t++) M[(size_t)(a * np + q) * m + b * np + t] = B[q * np + t];
+            }
+        }
+        if (invert_block(m, M, L->pinv[part] + (size_t)pi * m * m)) { free(M); return 1; }
+    }
+    free(M);
+    return 0;
 }
 
 /* child index and parent of fine cell K on level lev */
@@ -570,8 +680,9 @@ void orc_destroy(void *h) {
     for (int l = 0; l < S->nlev; l++) {
         olevel *L = &S->lv[l];
         void *p[] = {L->nbr, L->blk, L->inv, L->W, L->Z, L->alpha, L->x0, L->r0, L->x, L->r,
-                     L->z, L->w, L->t, L->bc, L->xc};
-        for (int i = 0; i < 15; i++) free(p[i]);
+                     L->z, L->w, L->t, L->bc, L->xc, L->pcell[0], L->pcell[1], L->pinv[0],
+                     L->pinv[1]};
+        for (int i = 0; i < 19; i++) free(p[i]);
     }
     free(S->P); free(S->Lc); free(S->piv); free(S);
 }
@@ -707,6 +818,20 @@ int orc_basis_size(void *h, int lev) { return ((osolver *)h)->lv[lev].l; }
 int orc_restarts(void *h) { return ((osolver *)h)->restarts; }
 /* m > 0: level 0 runs Alg. AsyncMG with m smoother steps per cycle; 0: Alg. 2 */
 void orc_set_async(void *h, int m) { ((osolver *)h)->async_m = m > 0 ? m : 0; }
+/* smoother of every iterated level: 0 Alg. BJ, 1 Alg. AS (builds the patches and their
+   inverses on first use); returns 0, or 1 if a patch matrix is singular */
+int orc_set_smoother(void *h, int kind) {
+    osolver *S = h;
+    if (kind == 1) {
+        if (S->nchild * S->np > 8 * 32) return 1;
+        for (int l = 0; l + 1 < S->nlev; l++)
+            if (!S->lv[l].pcell[0])
+                for (int part = 0; part < 2; part++)
+                    if (build_patches(S, l, part)) return 1;
+    }
+    S->smoother = kind == 1 ? 1 : 0;
+    return 0;
+}
 /* threads of the OpenMP build's parallel loops (n <= 0: all host cores); returns the
    number in use, 1 for the serial build */
 int orc_threads(int n) {

@@ -71,6 +71,8 @@ def _load(openmp: bool = False):
             lib.orc_grad_lognu.argtypes = [C.c_int, C.c_int, _ip, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
             lib.orc_threads.restype = C.c_int
             lib.orc_threads.argtypes = [C.c_int]
+            lib.orc_set_smoother.restype = C.c_int
+            lib.orc_set_smoother.argtypes = [C.c_void_p, C.c_int]
             _libs[openmp] = lib
     return _libs[openmp]
 
@@ -96,7 +98,7 @@ class OracleSolver:
 
     def __init__(self, dim, np_, n, nlevels, blocks, prolong, omega=0.7, sweeps=5,
                  lvl_rtol=None, lvl_maxit=None, lmax=0, transpose=False, async_smooth=0,
-                 openmp=False):
+                 openmp=False, smoother="bj"):
         self._lib = _load(openmp)
         rt, mi = default_level_criteria(nlevels)
         if lvl_rtol is not None:
@@ -116,6 +118,11 @@ class OracleSolver:
             raise RuntimeError(f"oracle setup failed with status {st.value}")
         # level 0 as Alg. AsyncMG with async_smooth smoother steps per cycle (0: Alg. 2)
         self._lib.orc_set_async(self._h, int(async_smooth))
+        # smoother of every iterated level: "bj" (Alg. BJ) or "as" (Alg. AS, cell patches)
+        if smoother not in ("bj", "as"):
+            raise ValueError("smoother must be 'bj' or 'as'")
+        if self._lib.orc_set_smoother(self._h, 1 if smoother == "as" else 0):
+            raise RuntimeError("oracle: a Schwarz patch matrix is singular or too large")
 
     @classmethod
     def from_problem(cls, pr, **kw):

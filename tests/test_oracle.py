@@ -431,3 +431,90 @@ def test_openmp_build_gives_bitwise_the_serial_results(m):
     assert np.array_equal(x0, x1)
     assert np.array_equal(i0["hist"], i1["hist"]) and i0["iters"] == i1["iters"]
     assert np.array_equal(i0["level_iters"], i1["level_iters"])
+
+
+# ------------------------------------------------------------------ Alg. AS (additive Schwarz)
+def _patch_dofs(pr, part):
+    """DOF index sets of the 2^d-cell patches of one partition, enumerated here from the
+    grid alone: partition 0 = the aligned 2^d blocks, partition 1 = the blocks shifted by
+    one cell in every direction (clipped at the boundary)."""
+    n = list(pr.n) + [1] * (3 - len(pr.n))
+    d, np_ = pr.d, pr.np_
+    ranges = [range(n[j] // 2 + part) if j < d else range(1) for j in range(3)]
+    out = []
+    for pz in ranges[2]:
+        for py in ranges[1]:
+            for px in ranges[0]:
+                cells = []
+                for cz in ([0, 1] if d == 3 else [0]):
+                    for cy in (0, 1):
+                        for cx in (0, 1):
+                            x, y = 2 * px - part + cx, 2 * py - part + cy
+                            z = 2 * pz - part + cz if d == 3 else 0
+                            if 0 <= x < n[0] and 0 <= y < n[1] and 0 <= z < n[2]:
+                                cells.append(x + n[0] * (y + n[1] * z))
+                out.append(np.concatenate([np.arange(K * np_, (K + 1) * np_) for K in cells]))
+    return out
+
+
+def _dense_as(A, pr, b, omega, sweeps):
+    """Additive Schwarz iterations from x = 0 written with dense submatrices and LU solves."""
+    x = np.zeros_like(b)
+    parts = [_patch_dofs(pr, 0), _patch_dofs(pr, 1)]
+    for _ in range(sweeps):
+        r = b - A @ x
+        e = np.zeros_like(b)
+        for patches in parts:
+            for idx in patches:
+                e[idx] += np.linalg.solve(A[np.ix_(idx, idx)], r[idx])
+        x = x + omega * e
+    return x
+
+
+@pytest.mark.parametrize("shape", [(2, 1, (8, 8)), (3, 1, (4, 4, 4)), (3, 2, (4, 4, 4)), (3, 2, (6, 6, 2))])
+@pytest.mark.parametrize("sweeps", [1, 2])
+def test_schwarz_smoother_matches_dense_patch_solves(shape, sweeps):
+    """Alg. AS on two partitions of overlapping 2^d-cell patches against the same
+    iteration built from dense submatrices A[idx, idx] and LU solves."""
+    d, p, n = shape
+    pr = make_problem(d, p, n, 2, seed=3)
+    A = dense_matrix(pr.blocks, pr.nbr)
+    orc = _solver(pr, smoother="as", omega=0.4, sweeps=sweeps)
+    x = orc.smooth(0, pr.b)
+    ref = _dense_as(A, pr, pr.b, 0.4, sweeps)
+    assert np.abs(x - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_schwarz_smoother_on_decoupled_cells_has_closed_form():
+    """With every face coupling removed, each patch solve is D^-1 on its cells and every
+    cell lies in one patch of each partition: k sweeps give (1 - (1 - 2 omega)^k) D^-1 b."""
+    pr = make_problem(3, 2, (4, 4, 4), 2, seed=5)
+    blocks = pr.blocks.copy()
+    blocks[1:] = 0.0
+    omega, k = 0.3, 3
+    orc = OracleSolver(pr.d, pr.np_, pr.n, 2, blocks, pr.prolong, omega=omega, sweeps=k, smoother="as")
+    x = orc.smooth(0, pr.b)
+    C, np_ = blocks.shape[1], pr.np_
+    dinv_b = np.concatenate([np.linalg.solve(blocks[0, K], pr.b[K * np_:(K + 1) * np_]) for K in range(C)])
+    ref = (1.0 - (1.0 - 2 * omega) ** k) * dinv_b
+    assert np.abs(x - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("m", [0, 4])
+def test_schwarz_smoothed_kcycle_matches_dense_lu(m):
+    pr = workload("sipg3d_p2_8cube").make(0)
+    A = dense_matrix(pr.blocks, pr.nbr)
+    xs = np.linalg.solve(A, pr.b)
+    x, info = _solver(pr, smoother="as", omega=0.5, sweeps=2, async_smooth=m).solve(pr.b, rtol=1e-10)
+    assert info["status"] == ORC_OK
+    assert np.linalg.norm(pr.b - A @ x) <= 1e-10 * np.linalg.norm(pr.b)
+    assert np.linalg.norm(x - xs) <= 1e-8 * np.linalg.norm(xs)
+
+
+def test_schwarz_openmp_build_gives_bitwise_the_serial_results():
+    import oracle
+    oracle.threads(4)
+    pr = make_problem(3, 2, (8, 8, 8), 3, seed=4)
+    out = [_solver(pr, smoother="as", omega=0.5, sweeps=2, openmp=o).solve(pr.b, rtol=1e-10)[0]
+           for o in (False, True)]
+    assert np.array_equal(out[0], out[1])

@@ -50,6 +50,9 @@ UNIT = "DOF/s"
 # HEADLINE_ASYNC_M smoother + RM steps per cycle beside the coarse path; the multiplicative
 # K-cycle of Alg. 2 (async 0) and the mixed forms are reported beside it.
 HEADLINE_ASYNC_M = 12
+# the additive Schwarz smoother of the Schwarz forms (Alg. AS on 2^d-cell patches)
+AS_OMEGA = 0.5
+AS_SWEEPS = 2
 # Level-0 cycles and level-1 iterations of the headline FP64 solve of this workload (seed 0,
 # LMAX = 400, m = 12), measured on GB300; the reference arm (a separate process)
 # extrapolates its bounded sample with them.
@@ -511,15 +514,20 @@ def main():
     # the other forms: one timed solve each, after the solve that captures its graph
     forms = {}
     if not args.no_mixed:
-        plan = [("fp64", 0), ("mixed", HEADLINE_ASYNC_M), ("mixed_bf16", HEADLINE_ASYNC_M),
-                ("ir32", HEADLINE_ASYNC_M), ("ir32_bf16", HEADLINE_ASYNC_M)]
+        # (precision, level-0 cycle m, smoother); the Schwarz forms run Alg. AS with
+        # omega 0.5 and 2 sweeps per smoother call
+        plan = [("fp64", 0, "bj"), ("mixed", HEADLINE_ASYNC_M, "bj"),
+                ("mixed_bf16", HEADLINE_ASYNC_M, "bj"), ("fp64", HEADLINE_ASYNC_M, "as"),
+                ("mixed_bf16", HEADLINE_ASYNC_M, "as"),
+                ("ir32", HEADLINE_ASYNC_M, "bj"), ("ir32_bf16", HEADLINE_ASYNC_M, "bj")]
         if args.all_forms:
-            plan += [("mixed", 0), ("mixed_bf16", 0)]
-        for prec, am in plan:
-            if prec == "fp64" and am == head_m:
+            plan += [("mixed", 0, "bj"), ("mixed_bf16", 0, "bj")]
+        for prec, am, smoother in plan:
+            if prec == "fp64" and am == head_m and smoother == "bj":
                 continue
+            skw = dict(smoother="as", omega=AS_OMEGA, sweeps=AS_SWEEPS) if smoother == "as" else {}
             sm = pkg.KCycleSolver(pr, precision=prec, use_graph=True, lmax=LMAX,
-                                  stream=stream.cuda_stream, async_smooth=am)
+                                  stream=stream.cuda_stream, async_smooth=am, **skw)
             solve(sm, b, x, maxiter=1)   # capture the graph
             sm.kernel_report()
             torch.cuda.synchronize()
@@ -531,6 +539,8 @@ def main():
             rp = sm.kernel_report(reps=10)
             sw_peak = hbm_peak if prec != "fp64" else fp64_gbs
             fname = (f"{prec}_multiplicative" if am == 0 else f"{prec}_task_parallel_m{am}")
+            if smoother == "as":
+                fname += "_schwarz"
             ir = prec.startswith("ir32")
             if ir:
                 dtype = ("f64 iterative refinement (compensated f64 residual) around an f32 inner "
@@ -551,6 +561,9 @@ def main():
                 "cycle": ("Alg. 2 (multiplicative K-cycle)" if am == 0 else
                           f"Alg. AsyncMG on level 0: coarse path on a second stream, {am} smoother "
                           f"+ RM steps per cycle beside it"),
+                "smoother": ("Alg. AS: additive Schwarz on two partitions of overlapping 2^d-cell "
+                             f"patches, omega {AS_OMEGA}, {AS_SWEEPS} sweeps" if smoother == "as"
+                             else "Alg. BJ: block Jacobi, omega 0.7, 5 sweeps"),
                 "smoother_sweep": {"bound": "hbm" if prec != "fp64" else "alu",
                                    "achieved": rp["sweep_bytes"] / (rp["sweep_ms"] * 1e-3) / 1e9,
                                    "peak": sw_peak, "unit": "GB/s",

@@ -119,6 +119,17 @@ typedef struct {
     int ir_max_steps;        /* KCMG_IR32*: cap on FP64 refinement steps (default 64) */
     int ir_inner_maxit;      /* KCMG_IR32*: cap on level-0 cycles of one inner solve (default
                                 300; the solve's maxiter caps their sum) */
+    int smoother;            /* smoother of every iterated level: 0 (default) the block
+                                Jacobi of Alg. BJ; 1 the additive Schwarz of Alg. AS on
+                                overlapping 2^d-cell patches (Sec. 3.2): the 2^d blocks of two
+                                partitions of the cells, one aligned with the agglomeration
+                                and one shifted by a cell in every direction, each patch's
+                                local matrix inverted densely at setup (in the smoother's
+                                precision: FP64, FP32, or BF16 in the *_BF16INV forms);
+                                a sweep is x += omega (z_0 + z_1) with z_k the patch solutions
+                                of partition k for the residual b - A x.  omega and sweeps
+                                as above (0.5 and 2 are typical).  Single right-hand side
+                                solves only. */
 } kcmg_params;
 
 /* Fill p with the defaults of Sec. 4.2 / Alg. BJ for the given sizes (blocks, prolong

@@ -12,6 +12,7 @@
 #pragma once
 #include "kcmg_internal.h"
 #include "reduce.cuh"
+#include "schwarz.cuh"
 
 #include <cuda/atomic>
 
@@ -128,6 +129,7 @@ struct CoarseCycle {
   double* sh;      // 32 doubles
   double* red_s;   // reduced sums (shared), >= kCoarseMaxCols
   TS* tile;        // blockDim TS (smoother exchange)
+  TS* as_rs;       // (blockDim / 32) x 2^d np TS: a warp's gathered patch residual (Alg. AS)
   T* Ps;           // NCH*NP*NP (prolongation matrices)
   double* cw;      // coefficient vectors in shared memory: 2 * kCoarseMaxCols
   int rcount = 0;  // reductions done (selects the partial buffer)
@@ -300,9 +302,79 @@ struct CoarseCycle {
     }
   }
 
-  // z = BJ(r) from z = 0 (a.sweeps sweeps); returns the FP64 correction C.z
+  // Alg. AS phases on a level (schwarz.cuh): the sweep's residual in TS, both partitions'
+  // patch solves (one warp per patch), and the combination z_new = z_old + omega (z_0 + z_1)
+  __device__ void as_residual(const CoarseLevel& C, const T* r, const TS* zo, bool first) {
+    count((double)C.N * (sizeof(T) + sizeof(TS)) + (first ? 0.0 : opbytes(C, S, a.smoother_bytes) + (double)C.N * sizeof(TS)));
+    const TS* A = static_cast<const TS*>(C.As);
+    TS* res = static_cast<TS*>(C.as_r);
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < C.N; row += gridDim.x * blockDim.x) {
+      TS v = (TS)ldv(r + row);
+      if (!first) {
+        const int g = row >> 5, lane = row & 31, K = row / NP;
+        TS acc[4] = {TS(0), TS(0), TS(0), TS(0)};
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          const int J = (s == 0) ? K : __ldg(C.nbr + (size_t)K * NF + s - 1);
+          if (J < 0) continue;
+          const VS2* Ap = reinterpret_cast<const VS2*>(A) + ((size_t)(s * C.G + g) * JP) * 32 + lane;
+          const TS* zp = zo + (size_t)J * NP;
+          const int c = (s & 1) << 1;
+#pragma unroll
+          for (int jp = 0; jp < JP; ++jp) {
+            const VS2 av = __ldg(Ap + jp * 32);
+            acc[c] = fma(av.x, ldv(zp + 2 * jp), acc[c]);
+            if (2 * jp + 1 < NP) acc[c + 1] = fma(av.y, ldv(zp + 2 * jp + 1), acc[c + 1]);
+          }
+        }
+        v -= (acc[0] + acc[1]) + (acc[2] + acc[3]);
+      }
+      res[row] = v;
+    }
+  }
+  __device__ void as_patches(const CoarseLevel& C) {
+    constexpr int M = NCH * NP;
+    const int np0 = as_npatch(C.n, DIM, 0), np1 = as_npatch(C.n, DIM, 1);
+    count((double)(np0 + np1) * M * M * a.inverse_bytes + (double)(np0 + np1) * M * 2 * sizeof(TS));
+    const TI* inv0 = static_cast<const TI*>(C.as_inv0);
+    const TI* inv1 = static_cast<const TI*>(C.as_inv1);
+    const TS* res = static_cast<const TS*>(C.as_r);
+    TS* zP = static_cast<TS*>(C.as_z);
+    const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    TS* rs = as_rs + (size_t)warp * M;
+    for (int w = blockIdx.x * wpb + warp; w < np0 + np1; w += gridDim.x * wpb) {
+      if (w < np0) as_patch_solve_warp<TS, TI, NP, DIM>(C.n, 0, w, inv0, res, zP, rs);
+      else as_patch_solve_warp<TS, TI, NP, DIM>(C.n, 1, w - np0, inv1, res, zP + (size_t)np0 * M, rs);
+    }
+  }
+  template <typename TO>
+  __device__ void as_combine(const CoarseLevel& C, const TS* zo, TO* zn, bool first) {
+    count((double)C.N * (2 * sizeof(TS) + sizeof(TO)));
+    const int np0 = as_npatch(C.n, DIM, 0);
+    const TS* zP = static_cast<const TS*>(C.as_z);
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < C.N; row += gridDim.x * blockDim.x)
+      zn[row] = (TO)as_combine_row<TS, NP, DIM>(C.n, row, zP, np0, zo, (TS)a.omega, first);
+  }
+
+  // z = BJ(r) or AS(r) from z = 0 (a.sweeps sweeps); returns the correction C.z (type T)
   __device__ T* smooth(int lev, const T* r) {
     const CoarseLevel& C = L(lev);
+    if (a.smoother == 1) {
+      TS* sb[2] = {static_cast<TS*>(C.s0), static_cast<TS*>(C.s1)};
+      T* out = vec(C.z);
+      for (int k = 0; k < a.sweeps && ok; ++k) {
+        const TS* zo = sb[(k + 1) & 1];
+        as_residual(C, r, zo, k == 0);
+        if (!(ok = bar())) break;
+        as_patches(C);
+        if (!(ok = bar())) break;
+        if (k == a.sweeps - 1) as_combine<T>(C, zo, out, k == 0);
+        else as_combine<TS>(C, zo, sb[k & 1], k == 0);
+        ok = bar();
+        ph(PH_SWEEP);
+      }
+      return out;
+    }
     TS* sb[2] = {static_cast<TS*>(C.s0), static_cast<TS*>(C.s1)};
     T* out = vec(C.z);
     for (int k = 0; k < a.sweeps && ok; ++k) {
@@ -672,7 +744,9 @@ __global__ void __launch_bounds__(320, KCMG_CC_MINBLOCKS) k_coarse_cycle(CoarseA
   const double* P = static_cast<const double*>(a.P);   // FP64 prolongation matrices
   for (int i = threadIdx.x; i < NCH * NP * NP; i += blockDim.x) Ps[i] = (T)P[i];
   __syncthreads();
-  CoarseCycle<TV, TS, TI, NP, DIM> cc{a, sh, red_s, tile, Ps, cw};
+  constexpr int M_AS = NCH * NP;
+  TS* as_rs = tile + blockDim.x;            // (blockDim / 32) warps x M_AS
+  CoarseCycle<TV, TS, TI, NP, DIM> cc{a, sh, red_s, tile, as_rs, Ps, cw};
   unsigned long long t0 = 0;
   if (blockIdx.x == 0 && threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
   // start of MG on the first coarse level: b, r, x were set by the restriction kernel

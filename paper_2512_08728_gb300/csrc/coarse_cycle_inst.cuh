@@ -25,7 +25,10 @@ static void* coarse_kernel_ptr(int np, int dim) {
 }
 
 static size_t coarse_cycle_smem(int np, int dim, int threads) {
-  return (size_t)threads * sizeof(CC_T) + (size_t)(1 << dim) * np * np * sizeof(CC_TV);
+  // prolongation matrices (CC_TV), the smoother tile (threads x CC_T), and one gathered
+  // patch residual per warp for the Schwarz smoother ((threads / 32) x 2^d np x CC_T)
+  return (size_t)(1 << dim) * np * np * sizeof(CC_TV) + (size_t)threads * sizeof(CC_T) +
+         (size_t)(threads / 32) * (1 << dim) * np * sizeof(CC_T);
 }
 
 template <>

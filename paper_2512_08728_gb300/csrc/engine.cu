@@ -3,6 +3,7 @@
 // refinement around an FP32 cycle, and the CUDA-graph form of the cycle in which every
 // level's while loop is a conditional while node driven by device-side state.
 #include "kcmg_internal.h"
+#include "schwarz.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -32,6 +33,9 @@ struct Level {
        *wre = nullptr, *W = nullptr, *Z = nullptr;
   // mixed forms: FP32 buffers of the smoother sweeps (the level's vectors are FP64)
   float *r_lo = nullptr, *z_lo = nullptr, *t_lo = nullptr;
+  // additive Schwarz smoother (Alg. AS): transposed patch inverses of partitions 0 and 1,
+  // patch solutions and the sweep's residual, all in the smoother's precision
+  void *as_inv0 = nullptr, *as_inv1 = nullptr, *as_z = nullptr, *as_r = nullptr;
   int lcap = 0;
   int nblk = 1;                     // blocks of the multi-column dot kernels
   int nblk2 = 1;                    // blocks of the update / finish / norm kernels
@@ -240,6 +244,59 @@ void build_hierarchy(kcmg_ctx* ctx, const double* blocks_src) {
     }
     CK(cudaGetLastError());
   }
+  // additive Schwarz smoother: patch inverses of every iterated level (FP64 Gauss-Jordan,
+  // then stored in the smoother's precision)
+  if (ctx->p.smoother == 1) {
+    const int m = (1 << dim) * np;
+    const bool bf16 = ctx->p.precision == KCMG_MIXED_BF16INV || ctx->p.precision == KCMG_IR32_BF16INV;
+    size_t maxp = 0;
+    for (int l = 0; l + 1 < ctx->nlev; ++l)
+      for (int part = 0; part < 2; ++part) {
+        const size_t c = (size_t)as_npatch(ctx->lv[l].n, dim, part);
+        if (c > maxp) maxp = c;
+      }
+    double* tmp = nullptr;   // FP64 inverses of one partition before conversion
+    if (ctx->mixed) CK(cudaMalloc(&tmp, maxp * m * m * sizeof(double)));
+    try {
+      for (int l = 0; l + 1 < ctx->nlev; ++l) {
+        Level& L = ctx->lv[l];
+        for (int part = 0; part < 2; ++part) {
+          const size_t cnt = (size_t)as_npatch(L.n, dim, part) * m * m;
+          double* inv64 = ctx->mixed ? tmp : dalloc<double>(ctx, cnt);
+          CK(cudaMemsetAsync(ctx->dflag, 0, sizeof(int), ctx->s));
+          CK(launch_patch_inverse(np, dim, L.nat, L.nbr, L.n, part, inv64, ctx->dflag, ctx->s));
+          int fail = 0;
+          CK(cudaMemcpyAsync(&fail, ctx->dflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+          CK(cudaStreamSynchronize(ctx->s));
+          if (fail) {
+            set_err(ctx, "a Schwarz patch matrix of level %d is singular", l);
+            throw Fail{KCMG_SINGULAR};
+          }
+          void* dst = inv64;
+          if (ctx->mixed && bf16) {
+            __nv_bfloat16* b16 = dalloc<__nv_bfloat16>(ctx, cnt);
+            launch_convert<double, __nv_bfloat16>(inv64, b16, cnt, ctx->s);
+            dst = b16;
+          } else if (ctx->mixed) {
+            float* f32 = dalloc<float>(ctx, cnt);
+            launch_convert<double, float>(inv64, f32, cnt, ctx->s);
+            dst = f32;
+          }
+          CK(cudaGetLastError());
+          CK(cudaStreamSynchronize(ctx->s));   // tmp is reused by the next partition
+          (part == 0 ? L.as_inv0 : L.as_inv1) = dst;
+        }
+        const size_t nz = ((size_t)as_npatch(L.n, dim, 0) + as_npatch(L.n, dim, 1)) * m;
+        const size_t es = ctx->mixed ? sizeof(float) : sizeof(double);
+        L.as_z = dalloc<char>(ctx, nz * es);
+        L.as_r = dalloc<char>(ctx, (size_t)L.N * es);
+      }
+    } catch (...) {
+      if (tmp) cudaFree(tmp);
+      throw;
+    }
+    if (tmp) cudaFree(tmp);
+  }
   // dense inverse of the coarsest operator (Gauss-Jordan with partial pivoting)
   Level& C = ctx->lv[ctx->nlev - 1];
   const int n = C.N;
@@ -310,8 +367,43 @@ struct Cycle {
     return e;
   }
 
+  // Alg. AS in T on buffers z/t: per sweep the residual r - A z_old (skipped on the first
+  // sweep from z = 0), both partitions' patch solves, and z_new = z_old + omega (z_0 + z_1)
+  T* as_sweeps(const Level& L, const T* r, T* z, T* t, cudaStream_t s) {
+    T* buf[2] = {z, t};
+    T* res = static_cast<T*>(L.as_r);
+    T* zp = static_cast<T*>(L.as_z);
+    const double om = ctx->p.omega;
+    const int sw = ctx->p.sweeps;
+    const bool bf16 = ctx->p.precision == KCMG_MIXED_BF16INV || ctx->p.precision == KCMG_IR32_BF16INV;
+    for (int k = 0; k < sw; ++k) {
+      T* out = buf[k & 1];
+      const T* old = buf[(k + 1) & 1];
+      const T* rk = r;
+      if (k > 0) {
+        launches += 1;
+        launch_spmv<T>(ctx->np, ctx->dim, Ainner(L), L.nbr, L.N, L.G, L.rows_pad, L.block_rows, old, res, r,
+                       nullptr, EpiArgs{}, 0, s);
+        rk = res;
+      }
+      launches += 2;
+      if (std::is_same<T, double>::value)
+        launch_as_patch<double, double>(ctx->np, ctx->dim, L.n, (const double*)L.as_inv0, (const double*)L.as_inv1,
+                                        (const double*)rk, (double*)zp, s);
+      else if (bf16)
+        launch_as_patch<float, __nv_bfloat16>(ctx->np, ctx->dim, L.n, (const __nv_bfloat16*)L.as_inv0,
+                                              (const __nv_bfloat16*)L.as_inv1, (const float*)rk, (float*)zp, s);
+      else
+        launch_as_patch<float, float>(ctx->np, ctx->dim, L.n, (const float*)L.as_inv0, (const float*)L.as_inv1,
+                                      (const float*)rk, (float*)zp, s);
+      launch_as_combine<T>(ctx->np, ctx->dim, L.n, L.N, zp, old, out, om, k == 0, s);
+    }
+    return buf[(sw - 1) & 1];
+  }
+
   // the smoother sweeps in T on buffers z/t; returns the buffer holding the result
   T* sweeps(const Level& L, const T* r, T* z, T* t, cudaStream_t s) {
+    if (ctx->p.smoother == 1) return as_sweeps(L, r, z, t, s);
     T* buf[2] = {z, t};
     const double om = ctx->p.omega;
     const int sw = ctx->p.sweeps;
@@ -954,6 +1046,7 @@ kcmg_ctx* build_ctx(const kcmg_params* p, cudaStream_t user, const double* block
               "n[%d] = %d is not divisible by 2^(nlevels-1)", j, p->n[j]);
     REQUIRE(p->lmax >= 0 && p->lmax <= kLcapMax - 3, "lmax must be in [0, %d]", kLcapMax - 3);
     REQUIRE(p->async_smooth >= 0 && p->async_smooth <= 64, "async_smooth must be in [0, 64]");
+    REQUIRE(p->smoother == 0 || p->smoother == 1, "smoother must be 0 (block Jacobi) or 1 (additive Schwarz)");
     ctx->dim = p->dim;
     ctx->np = p->np;
     ctx->S = 2 * p->dim + 1;
@@ -1102,7 +1195,12 @@ kcmg_ctx* build_ctx(const kcmg_params* p, cudaStream_t user, const double* block
         c.maxit = p->lvl_maxit[l];
         c.rtol = p->lvl_rtol[l];
         c.st = L.st;
+        c.as_inv0 = L.as_inv0;
+        c.as_inv1 = L.as_inv1;
+        c.as_z = L.as_z;
+        c.as_r = L.as_r;
       }
+      a.smoother = p->smoother;
       a.Ainv = ctx->Ainv;
       a.Nc = ctx->Nc;
       ctx->stat_ns = dalloc<unsigned long long>(ctx, 1);
@@ -1232,6 +1330,7 @@ kcmg_status kcmg_solve(kcmg_ctx* ctx, const double* b, double* x, int nrhs, doub
     REQUIRE(nrhs >= 1 && nrhs <= kMaxRhs, "nrhs must be in [1, %d]", kMaxRhs);
     REQUIRE(rtol >= 0 && atol >= 0 && maxiter >= 0, "negative tolerance or maxiter");
     REQUIRE(nrhs == 1 || !ctx->ir, "batched solves (nrhs > 1) support the FP64 and mixed forms");
+    REQUIRE(nrhs == 1 || ctx->p.smoother == 0, "batched solves (nrhs > 1) use the block-Jacobi smoother");
     if (nrhs > 1) return solve_multi(ctx, b, x, nrhs, rtol, atol, maxiter, info);
     return solve_impl(ctx, b, x, rtol, atol, maxiter, info);
   });
@@ -1493,10 +1592,49 @@ kcmg_status kcmg_kernel_report(kcmg_ctx* ctx, int reps, double* out, int nout) {
         out[o] = ms / reps;
         out[o + 1] = (double)S * L.N * np * vb + 2.0 * L.N * vb;
         const double sb = ctx->mixed ? 4 : 8;
-        const double ib = !ctx->mixed ? 8 : (L.D16 ? 2 : 4);
+        const double ib = !ctx->mixed ? 8 : ((L.D16 || ctx->p.precision == KCMG_IR32_BF16INV) ? 2 : 4);
         if (ctx->mixed) {
           CK(cudaMemsetAsync(L.r_lo, 0, L.N * sizeof(float), ctx->s));
           CK(cudaMemsetAsync(L.t_lo, 0, L.N * sizeof(float), ctx->s));
+        }
+        if (ctx->p.smoother == 1) {
+          // one full Schwarz sweep: residual, both partitions' patch solves, combination
+          const bool b16 = ctx->p.precision == KCMG_MIXED_BF16INV || ctx->p.precision == KCMG_IR32_BF16INV;
+          const int m = (1 << ctx->dim) * np;
+          const double npat = (double)as_npatch(L.n, ctx->dim, 0) + as_npatch(L.n, ctx->dim, 1);
+          CK(cudaEventRecord(e0, ctx->s));
+          for (int k = 0; k < reps; ++k) {
+            if (!ctx->mixed) {
+              const double *r = static_cast<double*>(L.b), *zo = static_cast<double*>(L.t);
+              launch_spmv<double>(np, ctx->dim, L.A64, L.nbr, L.N, L.G, L.rows_pad, L.block_rows, zo,
+                                  static_cast<double*>(L.as_r), r, nullptr, EpiArgs{}, 0, ctx->s);
+              launch_as_patch<double, double>(np, ctx->dim, L.n, (const double*)L.as_inv0, (const double*)L.as_inv1,
+                                              static_cast<double*>(L.as_r), static_cast<double*>(L.as_z), ctx->s);
+              launch_as_combine<double>(np, ctx->dim, L.n, L.N, static_cast<double*>(L.as_z), zo,
+                                        static_cast<double*>(L.z), ctx->p.omega, 0, ctx->s);
+            } else {
+              launch_spmv<float>(np, ctx->dim, L.A32, L.nbr, L.N, L.G, L.rows_pad, L.block_rows, L.t_lo,
+                                 static_cast<float*>(L.as_r), L.r_lo, nullptr, EpiArgs{}, 0, ctx->s);
+              if (b16)
+                launch_as_patch<float, __nv_bfloat16>(np, ctx->dim, L.n, (const __nv_bfloat16*)L.as_inv0,
+                                                      (const __nv_bfloat16*)L.as_inv1, static_cast<float*>(L.as_r),
+                                                      static_cast<float*>(L.as_z), ctx->s);
+              else
+                launch_as_patch<float, float>(np, ctx->dim, L.n, (const float*)L.as_inv0, (const float*)L.as_inv1,
+                                              static_cast<float*>(L.as_r), static_cast<float*>(L.as_z), ctx->s);
+              launch_as_combine<float>(np, ctx->dim, L.n, L.N, static_cast<float*>(L.as_z), L.t_lo, L.z_lo,
+                                       ctx->p.omega, 0, ctx->s);
+            }
+          }
+          CK(cudaEventRecord(e1, ctx->s));
+          CK(cudaEventSynchronize(e1));
+          CK(cudaEventElapsedTime(&ms, e0, e1));
+          out[o + 2] = ms / reps;
+          // operator and r, x, residual; patch inverses and their gathered/solved vectors;
+          // the combination reads both patch solutions and x, writes x
+          out[o + 3] = (double)S * L.N * np * sb + 3.0 * L.N * sb + npat * m * m * ib + npat * m * 2 * sb +
+                       4.0 * L.N * sb;
+          return;
         }
         CK(cudaEventRecord(e0, ctx->s));
         for (int k = 0; k < reps; ++k) {

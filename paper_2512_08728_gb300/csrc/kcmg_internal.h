@@ -126,6 +126,16 @@ void launch_axpy_to_double(const T* e, double* x, size_t n, cudaStream_t s); // 
 void launch_scale_to_float(const double* src, float* dst, double a, size_t n, cudaStream_t s);
 void launch_axpy_scaled_to_double(const float* e, double* x, double a, size_t n, cudaStream_t s);
 
+// additive Schwarz smoother on cell patches (schwarz.cu, schwarz.cuh)
+cudaError_t launch_patch_inverse(int np, int dim, const double* nat, const int* nbr, const int* n, int part,
+                                 double* invT, int* fail, cudaStream_t s);
+template <typename T, typename TI>
+void launch_as_patch(int np, int dim, const int* n, const TI* inv0, const TI* inv1, const T* r, T* zP,
+                     cudaStream_t s);
+template <typename T>
+void launch_as_combine(int np, int dim, const int* n, int N, const T* zP, const T* xold, T* xnew,
+                       double omega, int first, cudaStream_t s);
+
 // setup kernels (FP64, natural layout [S][C][np][np])
 int launch_galerkin(int np, int dim, const double* Af, const int* nbrf, const int* nf,
                     const int* nc, const double* P, double* Ac, cudaStream_t s);
@@ -175,6 +185,10 @@ struct CoarseLevel {
   int lcap, maxit;
   double rtol;
   LevelState* st;       // iteration/restart counters for the report
+  // additive Schwarz smoother: transposed patch inverses of partitions 0 and 1 (stored like
+  // Dinv), patch solutions and the sweep's residual (smoother precision)
+  const void *as_inv0, *as_inv1;
+  void *as_z, *as_r;
 };
 
 struct CoarseArgs {
@@ -200,6 +214,7 @@ struct CoarseArgs {
   unsigned long long* stat_phase_ns;   // [kCoarsePhases] time spent in each kind of phase
   int smoother_bytes;          // bytes per element of the smoother operator
   int inverse_bytes;           // bytes per element of the stored block inverses
+  int smoother;                // 0 block Jacobi (Alg. BJ), 1 additive Schwarz (Alg. AS)
 };
 
 // TV: vectors, bases and the residual minimisation; T: smoother sweeps; TI: stored inverses

@@ -1273,6 +1273,7 @@ template void launch_restrict<float, double>(int, int, const int*, const int*, c
 template void launch_prolong<float, double>(int, int, const int*, const int*, const float*,
                                             const float*, double*, cudaStream_t);
 template void launch_convert<double, float>(const double*, float*, size_t, cudaStream_t);
+template void launch_convert<double, __nv_bfloat16>(const double*, __nv_bfloat16*, size_t, cudaStream_t);
 template void launch_convert<float, double>(const float*, double*, size_t, cudaStream_t);
 
 }  // namespace kcmg

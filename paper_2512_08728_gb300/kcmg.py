@@ -33,7 +33,7 @@ class kcmg_params(C.Structure):
                 ("precision", C.c_int), ("use_graph", C.c_int), ("coarse_persistent", C.c_int),
                 ("tc_tf32_only", C.c_int), ("async_smooth", C.c_int),
                 ("ir_inner_rtol", C.c_double), ("ir_max_steps", C.c_int),
-                ("ir_inner_maxit", C.c_int)]
+                ("ir_inner_maxit", C.c_int), ("smoother", C.c_int)]
 
 
 class kcmg_info(C.Structure):
@@ -338,7 +338,7 @@ class KCycleSolver:
     def __init__(self, problem, precision="fp64", use_graph=True, omega=0.7, sweeps=5,
                  lmax=0, lvl_rtol=None, lvl_maxit=None, coarse_persistent=True, stream=None,
                  tc_tf32_only=0, async_smooth=0, ir_inner_rtol=None, ir_max_steps=None,
-                 ir_inner_maxit=None):
+                 ir_inner_maxit=None, smoother="bj"):
         pr = problem
         self.dim, self.np_, self.nlevels = pr.d, pr.np_, pr.nlevels
         self.ndof = pr.ndof
@@ -355,6 +355,9 @@ class KCycleSolver:
             p.ir_max_steps = int(ir_max_steps)
         if ir_inner_maxit is not None:
             p.ir_inner_maxit = int(ir_inner_maxit)
+        if smoother not in ("bj", "as"):
+            raise ValueError("smoother must be 'bj' (Alg. BJ) or 'as' (Alg. AS)")
+        p.smoother = 1 if smoother == "as" else 0
         if lvl_rtol is not None:
             for i, v in enumerate(lvl_rtol):
                 p.lvl_rtol[i] = v

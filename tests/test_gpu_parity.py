@@ -451,3 +451,47 @@ def test_iterative_refinement_degenerate_inputs():
         s.solve(np.zeros((pr.ndof, 2)), rtol=1e-10)
     assert e.value.status == 5
     s.close()
+
+
+# ------------------------------------------------------------------ Alg. AS (additive Schwarz)
+AS_KW = dict(smoother="as", omega=0.5, sweeps=2)
+
+
+@pytest.mark.parametrize("name", SMALL + ["ragged_3d_p2"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 3e-5), ("mixed_bf16", 2e-2)])
+def test_schwarz_smoother(name, precision, tol):
+    """Alg. AS on the two partitions of overlapping 2^d-cell patches, every iterated level,
+    against the oracle's Alg. AS (dense local inverses in the smoother's precision)."""
+    pr = _problem(name)
+    orc = OracleSolver.from_problem(pr, **AS_KW)
+    s = pkg.KCycleSolver(pr, precision=precision, **AS_KW)
+    rng = np.random.default_rng(12)
+    for lev in range(pr.nlevels - 1):
+        r = rng.standard_normal(orc.ndof(lev))
+        assert _rel(s.smooth(lev, r), orc.smooth(lev, r)) < tol
+    s.close()
+
+
+@pytest.mark.parametrize("name", SMALL + ["ragged_3d_p2", "sipg2d_p1_32x32_5lev"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed_bf16"])
+@pytest.mark.parametrize("m,persistent", [(0, True), (0, False), (3, True)])
+def test_schwarz_smoothed_solve_matches_oracle(name, precision, m, persistent):
+    pr = _problem(name)
+    x_or, io = OracleSolver.from_problem(pr, async_smooth=m, **AS_KW).solve(pr.b, rtol=1e-10, maxiter=2000)
+    assert io["status"] == 0
+    s = pkg.KCycleSolver(pr, precision=precision, use_graph=True, coarse_persistent=persistent,
+                         async_smooth=m, **AS_KW)
+    x, info = s.solve(pr.b, rtol=RTOL_GPU, maxiter=2000)
+    s.close()
+    assert info["status"] == 0, info
+    _check_solution(pr, x, info, x_or)
+
+
+def test_schwarz_smoother_in_the_refinement_form():
+    pr = _problem("sipg3d_p2_8cube")
+    x_or, _ = OracleSolver.from_problem(pr, **AS_KW).solve(pr.b, rtol=1e-10, maxiter=400)
+    s = pkg.KCycleSolver(pr, precision="ir32", async_smooth=3, **AS_KW)
+    x, info = s.solve(pr.b, rtol=RTOL_GPU, maxiter=2000)
+    s.close()
+    assert info["status"] == 0, info
+    _check_solution(pr, x, info, x_or)

@@ -50,9 +50,15 @@ UNIT = "DOF/s"
 # HEADLINE_ASYNC_M smoother + RM steps per cycle beside the coarse path; the multiplicative
 # K-cycle of Alg. 2 (async 0) and the mixed forms are reported beside it.
 HEADLINE_ASYNC_M = 12
-# the additive Schwarz smoother of the Schwarz forms (Alg. AS on 2^d-cell patches)
+# the additive Schwarz smoother of the Schwarz forms (Alg. AS on 2^d-cell patches) and the
+# level-0 cycle each Schwarz form runs (best mean over seeds 0/1/2 on GB300)
 AS_OMEGA = 0.5
 AS_SWEEPS = 2
+AS_ASYNC_M_FP64 = 16
+AS_ASYNC_M_MIXED = 12
+# the stretched p = 3 workload of the mixed-precision configuration
+STRETCHED = "sipg3d_p3_48cube_zstretch"
+STRETCHED_ASYNC_M = 12
 # Level-0 cycles and level-1 iterations of the headline FP64 solve of this workload (seed 0,
 # LMAX = 400, m = 12), measured on GB300; the reference arm (a separate process)
 # extrapolates its bounded sample with them.
@@ -328,6 +334,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-stretched", action="store_true",
+                    help="skip the stretched p = 3 workload (48^3, 1:10 in z) of the mixed-precision forms")
     ap.add_argument("--all-forms", action="store_true",
                     help="also time the mixed forms with the multiplicative cycle (about 30 s each)")
     ap.add_argument("--async-m", type=int, default=None,
@@ -485,6 +493,19 @@ def main():
         alu_kernel("k_spmv", "FP64 operator application (Alg. 1: w = A z), levels 0 and 1",
                    (rep["spmv_ms"], rep["spmv1_ms"]), n_spmv, spmv_flop),
     ]
+    # Alg. 1's Gram kernels on level 0 (one launch of each per level-0 RM), timed at the
+    # basis length halfway through a restart period; level-1 launches are not counted
+    n_rm0 = cycles * rms0
+    for kname, key, what in (("k_gram_update", "gram_update", "Alg. 1 new column: w - W h, z - Z h (FP64), level 0"),
+                             ("k_gram_dots", "gram_dots", "Alg. 1 first Gram pass: W^T w, ||w||^2 (FP64), level 0")):
+        t, fl = rep[key + "_ms"], rep[key + "_flop"]
+        tf = fl / (t * 1e-3) / 1e12 if t > 0 else 0.0
+        kernels.append({"name": kname, "what": what, "bound": "alu", "achieved": tf, "peak": FP64_TFLOPS,
+                        "unit": "TFLOP/s", "frac": tf / FP64_TFLOPS, "launches_per_step": n_rm0,
+                        "ms_per_launch": t, "flop_per_launch": fl, "basis_length": rep["gram_l"],
+                        "share_of_step": n_rm0 * t / step_ms if step_ms > 0 else None,
+                        "timing": "standalone CUDA events per launch at the mid-restart basis length "
+                                  "x level-0 RMs per solve"})
     # the dominant kernel: the largest share of the solve among the kernels timed here
     dom = max(kernels, key=lambda k: k["share_of_step"] or 0.0)
     traffic, traffic_note = _traffic(dom["name"])
@@ -512,66 +533,84 @@ def main():
     s.close()
 
     # the other forms: one timed solve each, after the solve that captures its graph
+    def time_form(prob, bb, xx, prec, am, smoother, lmax=LMAX, maxiter=None):
+        skw = dict(smoother="as", omega=AS_OMEGA, sweeps=AS_SWEEPS) if smoother == "as" else {}
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sm = pkg.KCycleSolver(prob, precision=prec, use_graph=True, lmax=lmax,
+                              stream=stream.cuda_stream, async_smooth=am, **skw)
+        torch.cuda.synchronize()
+        setup = time.perf_counter() - t0
+        solve(sm, bb, xx, maxiter=1)   # capture the graph
+        sm.kernel_report()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        inf = solve(sm, bb, xx, maxiter=maxiter)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mms = e0.elapsed_time(e1)
+        rp = sm.kernel_report(reps=10)
+        sm.close()
+        ir = prec.startswith("ir32")
+        if ir:
+            dtype = ("f64 iterative refinement (compensated f64 residual) around an f32 inner "
+                     "K-cycle: f32 operators, sweeps, transfers, bases"
+                     + (", bf16 block inverses" if prec == "ir32_bf16" else "")
+                     + "; f64 Gram reductions and coarsest solve")
+        elif prec != "fp64":
+            dtype = ("f32 smoother sweeps" + (", bf16 block inverses" if prec == "mixed_bf16" else "")
+                     + "; f64 residual minimisation, transfers, coarsest solve")
+        else:
+            dtype = "f64"
+        sw_peak = hbm_peak if prec != "fp64" else fp64_gbs
+        return {
+            "value": prob.ndof / (mms * 1e-3), "unit": UNIT, "timed_solves": 1,
+            "ms_per_step": mms, "setup_s": setup, "status": inf["status"],
+            "rel_res": inf["rel_res"], "cycles": inf["iters"],
+            "refinements": inf["refinements"] if ir else None, "dtype": dtype,
+            "cycle": ("Alg. 2 (multiplicative K-cycle)" if am == 0 else
+                      f"Alg. AsyncMG on level 0: coarse path on a second stream, {am} smoother "
+                      f"+ RM steps per cycle beside it"), "lmax": lmax,
+            "smoother": ("Alg. AS: additive Schwarz on two partitions of overlapping 2^d-cell "
+                         f"patches, omega {AS_OMEGA}, {AS_SWEEPS} sweeps" if smoother == "as"
+                         else "Alg. BJ: block Jacobi, omega 0.7, 5 sweeps"),
+            "smoother_sweep": {"bound": "hbm" if prec != "fp64" else "alu",
+                               "achieved": rp["sweep_bytes"] / (rp["sweep_ms"] * 1e-3) / 1e9,
+                               "peak": sw_peak, "unit": "GB/s",
+                               "frac": rp["sweep_bytes"] / (rp["sweep_ms"] * 1e-3) / 1e9 / sw_peak,
+                               "ms_per_launch": rp["sweep_ms"]},
+            "coarse_cycle_gbs": (rp["coarse_bytes"] / max(1, rp["coarse_launches"]))
+                                / (rp["coarse_ms"] / max(1, rp["coarse_launches"]) * 1e-3) / 1e9
+                                if rp["coarse_ms"] > 0 else None}
+
     forms = {}
     if not args.no_mixed:
-        # (precision, level-0 cycle m, smoother); the Schwarz forms run Alg. AS with
-        # omega 0.5 and 2 sweeps per smoother call
+        # (precision, level-0 cycle m, smoother) on the benchmark workload; each form runs
+        # the level-0 cycle measured best for it over three seeds
         plan = [("fp64", 0, "bj"), ("mixed", HEADLINE_ASYNC_M, "bj"),
-                ("mixed_bf16", HEADLINE_ASYNC_M, "bj"), ("fp64", HEADLINE_ASYNC_M, "as"),
-                ("mixed_bf16", HEADLINE_ASYNC_M, "as"),
+                ("mixed_bf16", HEADLINE_ASYNC_M, "bj"), ("fp64", AS_ASYNC_M_FP64, "as"),
+                ("mixed_bf16", AS_ASYNC_M_MIXED, "as"),
                 ("ir32", HEADLINE_ASYNC_M, "bj"), ("ir32_bf16", HEADLINE_ASYNC_M, "bj")]
         if args.all_forms:
             plan += [("mixed", 0, "bj"), ("mixed_bf16", 0, "bj")]
         for prec, am, smoother in plan:
             if prec == "fp64" and am == head_m and smoother == "bj":
                 continue
-            skw = dict(smoother="as", omega=AS_OMEGA, sweeps=AS_SWEEPS) if smoother == "as" else {}
-            sm = pkg.KCycleSolver(pr, precision=prec, use_graph=True, lmax=LMAX,
-                                  stream=stream.cuda_stream, async_smooth=am, **skw)
-            solve(sm, b, x, maxiter=1)   # capture the graph
-            sm.kernel_report()
-            torch.cuda.synchronize()
-            e0.record(stream)
-            inf = solve(sm, b, x)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            mms = e0.elapsed_time(e1)
-            rp = sm.kernel_report(reps=10)
-            sw_peak = hbm_peak if prec != "fp64" else fp64_gbs
             fname = (f"{prec}_multiplicative" if am == 0 else f"{prec}_task_parallel_m{am}")
             if smoother == "as":
                 fname += "_schwarz"
-            ir = prec.startswith("ir32")
-            if ir:
-                dtype = ("f64 iterative refinement (compensated f64 residual) around an f32 inner "
-                         "K-cycle: f32 operators, sweeps, transfers, bases"
-                         + (", bf16 block inverses" if prec == "ir32_bf16" else "")
-                         + "; f64 Gram reductions and coarsest solve")
-            elif prec != "fp64":
-                dtype = ("f32 smoother sweeps" + (", bf16 block inverses" if prec == "mixed_bf16" else "")
-                         + "; f64 residual minimisation, transfers, coarsest solve")
-            else:
-                dtype = "f64"
-            forms[fname] = {
-                "value": pr.ndof / (mms * 1e-3), "unit": UNIT, "timed_solves": 1,
-                "ms_per_step": mms, "status": inf["status"],
-                "rel_res": inf["rel_res"], "cycles": inf["iters"],
-                "refinements": inf["refinements"] if ir else None,
-                "dtype": dtype,
-                "cycle": ("Alg. 2 (multiplicative K-cycle)" if am == 0 else
-                          f"Alg. AsyncMG on level 0: coarse path on a second stream, {am} smoother "
-                          f"+ RM steps per cycle beside it"),
-                "smoother": ("Alg. AS: additive Schwarz on two partitions of overlapping 2^d-cell "
-                             f"patches, omega {AS_OMEGA}, {AS_SWEEPS} sweeps" if smoother == "as"
-                             else "Alg. BJ: block Jacobi, omega 0.7, 5 sweeps"),
-                "smoother_sweep": {"bound": "hbm" if prec != "fp64" else "alu",
-                                   "achieved": rp["sweep_bytes"] / (rp["sweep_ms"] * 1e-3) / 1e9,
-                                   "peak": sw_peak, "unit": "GB/s",
-                                   "frac": rp["sweep_bytes"] / (rp["sweep_ms"] * 1e-3) / 1e9 / sw_peak},
-                "coarse_cycle_gbs": (rp["coarse_bytes"] / max(1, rp["coarse_launches"]))
-                                    / (rp["coarse_ms"] / max(1, rp["coarse_launches"]) * 1e-3) / 1e9
-                                    if rp["coarse_ms"] > 0 else None}
-            sm.close()
+            forms[fname] = time_form(pr, b, x, prec, am, smoother)
+        if not args.no_stretched and ws == 1:
+            # the mixed-precision configuration: 48^3 cells, p = 3, stretched 1:10 in z, nu
+            # 1:1e4 (block Jacobi stalls near 2e-4 on it; the Schwarz smoother converges)
+            p3 = workload(STRETCHED).make(rank)
+            b3 = torch.from_numpy(p3.b).to(dev)
+            x3 = torch.zeros_like(b3)
+            for prec in ("mixed", "fp64"):
+                f = time_form(p3, b3, x3, prec, STRETCHED_ASYNC_M, "as")
+                f["workload"] = STRETCHED
+                forms[f"{STRETCHED}_{prec}_task_parallel_m{STRETCHED_ASYNC_M}_schwarz"] = f
+            del b3, x3
 
     if args.mrhs:
         forms["mrhs32"] = run_mrhs(pkg, rank, dev, stream, hbm_peak, args)

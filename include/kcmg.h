@@ -230,7 +230,11 @@ kcmg_status kcmg_rm_sequence(kcmg_ctx *ctx, int level, const double *b, const do
    reduction, 2 second Gram pass, 3 new basis column with its norms, 4 normalisation and
    x, r update, 5 restriction or prolongation, 6 coarsest solve, 7 restart residual,
    8 level entry and return.  out[28..31] (if nout allows, reps > 0 and level 1 is iterated):
-   the same four timings as out[3..6] on level 1.  nout >= 7. */
+   the same four timings as out[3..6] on level 1.  out[32..36] (if nout allows, reps > 0):
+   the level-0 Gram kernels of Alg. 1 at the basis length halfway through a restart period:
+   ms and FLOPs of the first Gram pass, ms and FLOPs of the update of the new column, and
+   the basis length used (these calls overwrite the basis; the next solve starts afresh).
+   nout >= 7. */
 kcmg_status kcmg_kernel_report(kcmg_ctx *ctx, int reps, double *out, int nout);
 
 /* r = b - A x with the finest-level FP64 operator, and *rnorm = ||r|| (a host double),

@@ -1656,8 +1656,73 @@ kcmg_status kcmg_kernel_report(kcmg_ctx* ctx, int reps, double* out, int nout) {
         out[o + 3] = (double)(S - 1) * L.N * np * sb + (double)L.N * np * ib + 3.0 * L.N * sb;
       };
       time_level(0, 3);
-      if (ctx->nlev > 2 && nout >= 7 + KCMG_MAX_LEVELS + kCoarsePhases + 4)
-        time_level(1, 7 + KCMG_MAX_LEVELS + kCoarsePhases);
+      const int o1 = 7 + KCMG_MAX_LEVELS + kCoarsePhases;
+      if (ctx->nlev > 2 && nout >= o1 + 4) time_level(1, o1);
+      // the level-0 Gram kernels of Alg. 1 at the basis length halfway through a restart
+      // period: out[o1 + 4] ms and out[o1 + 5] FLOPs of the first Gram pass (W^T w, ||w||^2),
+      // out[o1 + 6], out[o1 + 7] of the new column's update (w - W h, z - Z h); out[o1 + 8]
+      // the basis length used.  The calls overwrite the level's basis scratch.
+      if (nout >= o1 + 9) {
+        Level& L = ctx->lv[0];
+        const int per = ctx->p.async_smooth > 0 ? ctx->p.async_smooth + 1 : 3;
+        const int cap = (ctx->p.lmax > 0 && ctx->p.lmax < L.lcap) ? ctx->p.lmax : L.lcap - per;
+        int lt = (cap + per) / 2;
+        if (lt > L.lcap - 1) lt = L.lcap - 1;
+        if (lt < 1) lt = 1;
+        LevelState h;
+        CK(cudaMemcpyAsync(&h, L.st, sizeof h, cudaMemcpyDeviceToHost, ctx->s));
+        CK(cudaStreamSynchronize(ctx->s));
+        h.l = lt;
+        h.flags = 0;
+        h.ticket = 0;
+        CK(cudaMemcpyAsync(L.st, &h, sizeof h, cudaMemcpyHostToDevice, ctx->s));
+        const size_t vb = ctx->ir ? sizeof(float) : sizeof(double);
+        CK(cudaMemsetAsync(L.w, 0, L.N * vb, ctx->s));
+        EpiArgs g1;
+        g1.st = L.st;
+        g1.kind = EPI_GRAM1;
+        g1.h = L.h;
+        g1.h2 = L.h2;
+        EpiArgs up = g1;
+        up.kind = EPI_UPDATE;
+        float ms = 0;
+        CK(cudaEventRecord(e0, ctx->s));
+        for (int k = 0; k < reps; ++k) {
+          if (ctx->ir)
+            launch_gram_dots<float>(static_cast<float*>(L.W), L.N, static_cast<float*>(L.w), L.lcap, L.nblk,
+                                    L.partial, g1, 0, ctx->s);
+          else
+            launch_gram_dots<double>(static_cast<double*>(L.W), L.N, static_cast<double*>(L.w), L.lcap, L.nblk,
+                                     L.partial, g1, 0, ctx->s);
+        }
+        CK(cudaEventRecord(e1, ctx->s));
+        CK(cudaEventSynchronize(e1));
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        out[o1 + 4] = ms / reps;
+        out[o1 + 5] = 2.0 * (lt + 1) * L.N;
+        // the first pass set the flags from zero vectors: clear them for a plain update
+        h.flags = 0;
+        CK(cudaMemcpyAsync(&L.st->flags, &h.flags, sizeof(int), cudaMemcpyHostToDevice, ctx->s));
+        CK(cudaEventRecord(e0, ctx->s));
+        for (int k = 0; k < reps; ++k) {
+          if (ctx->ir)
+            launch_gram_update<float>(static_cast<float*>(L.W), static_cast<float*>(L.Z), L.N,
+                                      static_cast<float*>(L.w), static_cast<float*>(L.wre),
+                                      static_cast<float*>(L.z), static_cast<float*>(L.r), L.lcap, L.nblk2,
+                                      L.partial, up, ctx->s);
+          else
+            launch_gram_update<double>(static_cast<double*>(L.W), static_cast<double*>(L.Z), L.N,
+                                       static_cast<double*>(L.w), static_cast<double*>(L.wre),
+                                       static_cast<double*>(L.z), static_cast<double*>(L.r), L.lcap, L.nblk2,
+                                       L.partial, up, ctx->s);
+        }
+        CK(cudaEventRecord(e1, ctx->s));
+        CK(cudaEventSynchronize(e1));
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        out[o1 + 6] = ms / reps;
+        out[o1 + 7] = 4.0 * lt * L.N;
+        out[o1 + 8] = lt;
+      }
       CK(cudaGetLastError());
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);

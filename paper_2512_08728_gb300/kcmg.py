@@ -260,7 +260,7 @@ def kcmg_kernel_report(ctx, reps=0):
     """Coarse-cycle kernel counters since the last call and, with reps > 0, CUDA-event
     timings of the level-0 operator application and smoother sweep (see kcmg.h)."""
     n0 = 7 + KCMG_MAX_LEVELS + len(COARSE_PHASES)
-    out = np.zeros(n0 + 4)
+    out = np.zeros(n0 + 9)
     _check(ctx, load_library().kcmg_kernel_report(ctx, int(reps), out.ctypes.data, out.size))
     ph = out[7 + KCMG_MAX_LEVELS:n0]
     return {"coarse_launches": int(out[0]), "coarse_ms": out[1], "coarse_bytes": out[2],
@@ -268,7 +268,9 @@ def kcmg_kernel_report(ctx, reps=0):
             "coarse_level_ms": out[7:7 + KCMG_MAX_LEVELS].tolist(),
             "coarse_phase_ms": dict(zip(COARSE_PHASES, ph.tolist())),
             "spmv1_ms": out[n0], "spmv1_bytes": out[n0 + 1], "sweep1_ms": out[n0 + 2],
-            "sweep1_bytes": out[n0 + 3]}
+            "sweep1_bytes": out[n0 + 3], "gram_dots_ms": out[n0 + 4], "gram_dots_flop": out[n0 + 5],
+            "gram_update_ms": out[n0 + 6], "gram_update_flop": out[n0 + 7],
+            "gram_l": int(out[n0 + 8])}
 
 
 def _unary(name, ctx, level, x, nout, *extra):

@@ -386,9 +386,14 @@ def test_benchmark_level_layout_32cube_task_parallel_matches_oracle(monkeypatch)
 
 
 # ------------------------------------------------------------------ FP64 refinement, FP32 inner solve
-@pytest.mark.parametrize("name", SMALL + ["ragged_3d_p2", "sipg2d_p1_32x32_5lev"])
-@pytest.mark.parametrize("precision", ["ir32", "ir32_bf16"])
-@pytest.mark.parametrize("m,persistent", [(0, True), (0, False), (3, True)])
+_IR_CASES = ([(n, "ir32", 0, True) for n in SMALL + ["ragged_3d_p2", "sipg2d_p1_32x32_5lev"]]
+             + [(n, "ir32", m, pers) for n in ("sipg3d_p2_8cube", "ragged_3d_p2", "sipg2d_p1_32x32_5lev")
+                for m, pers in ((0, False), (3, True))]
+             + [(n, "ir32_bf16", 0, True) for n in ("sipg2d_p1_16x16", "sipg3d_p2_8cube",
+                                                   "sipg3d_p3_8cube_zstretch")])
+
+
+@pytest.mark.parametrize("name,precision,m,persistent", _IR_CASES)
 def test_iterative_refinement_solve_matches_fp64_oracle(name, precision, m, persistent):
     """FP64 outer refinement around a K-cycle run entirely in FP32 (operators, sweeps,
     transfers, bases) with FP64 Gram reductions and coarsest solve: the FP64 true residual

@@ -87,10 +87,17 @@ FP64_PEAK_NOTE = ("FP64 FMA peak from unit counts and clock: 152 SMs x 2 FMA/clk
                   "2.07 GHz = %.3f TFLOP/s, i.e. %.0f GB/s of 8-byte operands at one FMA each"
                   % (FP64_TFLOPS, FP64_TFLOPS * 1e3 / 2 * 8))
 
-# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernels
-# the bench reports, from one ncu capture each, keyed by kernel; valid only while the
-# kernel's sources hash to the recorded value (otherwise the line reports null).
-TRAFFIC = {}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the kernels the bench
+# reports, from one ncu capture each, as bytes per unit of work (k_gram_update: per
+# (basis column + 2.5) x DOF, the unit its algorithmic bytes (2 l + 5) N 8 count), keyed by
+# kernel; valid only while the kernel's sources hash to the recorded value (otherwise the
+# line reports null).
+TRAFFIC = {
+    "k_gram_update": (3567740400.0 / ((2 * 199 + 5) * 1105920), "6b661e12a19f0e25",
+                      ["kernels.cu", "kcmg_internal.h", "reduce.cuh"],
+                      "ncu --set full capture of one level-0 launch on 48^3 p=2 with 199 basis "
+                      "vectors: 3.568 GB per launch, scaled to this launch by (2 l + 5) N"),
+}
 
 
 def _sources_sha(files):
@@ -334,6 +341,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--probe", choices=["rm", "smooth"], default=None,
+                    help="profiling runs only: on 48^3 p=2 (1.1M DOFs, 4 levels), 'rm' applies Alg. 1 "
+                         "to --probe-n random corrections on level 0 (the k-th RM orthogonalises "
+                         "against k - 1 vectors); 'smooth' runs three level-0 smoother calls and "
+                         "operator applications; then exits")
+    ap.add_argument("--probe-n", type=int, default=100)
+    ap.add_argument("--probe-precision", default="fp64")
     ap.add_argument("--no-stretched", action="store_true",
                     help="skip the stretched p = 3 workload (48^3, 1:10 in z) of the mixed-precision forms")
     ap.add_argument("--all-forms", action="store_true",
@@ -382,6 +396,25 @@ def main():
     hbm_peak, peak_kind = _peaks()
 
     stream = torch.cuda.current_stream()
+    if args.probe:
+        from workloads import make_problem
+        pp = make_problem(3, 2, (48, 48, 48), 4, seed=0)
+        sv = pkg.KCycleSolver(pp, precision=args.probe_precision,
+                              lmax=max(args.probe_n, 1), stream=stream.cuda_stream)
+        if args.probe == "rm":
+            zs = np.random.default_rng(1).standard_normal((args.probe_n, pp.ndof))
+            _, rr, ll = sv.rm_sequence(0, pp.b, np.zeros(pp.ndof), zs)
+            print(json.dumps({"probe": "rm", "basis": ll, "rnorm": float(np.linalg.norm(rr))}))
+        else:
+            rv = torch.from_numpy(pp.b).to(dev)
+            for _ in range(3):
+                zz = sv.smooth(0, rv)
+                yy = sv.apply(0, rv)
+            torch.cuda.synchronize()
+            print(json.dumps({"probe": "smooth", "z": float(torch.linalg.vector_norm(zz)),
+                              "y": float(torch.linalg.vector_norm(yy))}))
+        sv.close()
+        return
     if args.mrhs_only:
         out = run_mrhs(pkg, rank, dev, stream, hbm_peak, args)
         if rank == 0:
@@ -509,6 +542,8 @@ def main():
     # the dominant kernel: the largest share of the solve among the kernels timed here
     dom = max(kernels, key=lambda k: k["share_of_step"] or 0.0)
     traffic, traffic_note = _traffic(dom["name"])
+    if traffic is not None and dom["name"] == "k_gram_update":   # bytes per unit -> per launch
+        traffic = traffic * (2 * rep["gram_l"] + 5) * pr.ndof
 
     # end to end through the C interface with pinned host buffers: every step copies b
     # and x0 to the device and x back inside the timed region

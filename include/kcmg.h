@@ -269,7 +269,9 @@ kcmg_status kcmg_smooth_multi(kcmg_ctx *ctx, int level, int nrhs, const double *
    ctx: out[0] warps per block of the FP64 block SpMM, out[1] its time (ms), out[2] warps
    per block of the tensor-core sweep, out[3] its grid (0 = one warp per cell), out[4] its
    time (ms), out[5] level-0 basis capacity per column, out[6] nrhs, out[7] 1 if the
-   sweep splits each product into three TF32 products (tc_tf32_only = 0).  Zero-filled up to nout. */
+   sweep splits each product into three TF32 products (tc_tf32_only = 0), out[8] 1 if the
+   sweep stages each cell's blocks, inverse, r and neighbour slabs by double-buffered 1-D
+   bulk copies (chosen when it times faster).  Zero-filled up to nout. */
 kcmg_status kcmg_mrhs_tuning(kcmg_ctx *ctx, double *out, int nout);
 
 /* Level sizes: number of cells of a level (0 if out of range). */

@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -836,6 +837,283 @@ __global__ void k_restart_mask(const MState* st, int* mask) {
   if (r < kMaxRhs) mask[r] = (r < st->R) ? st->restart[r] : 0;
 }
 
+// ---- bulk-copy pipeline for the tensor-core sweep (cp.async.bulk + mbarrier, inline PTX)
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok = 0;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// 1-D bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+template <int NP, int S> struct TcbShape {
+  static constexpr int NF = S - 1;
+  // floats of one stage for R right-hand sides: blocks, inverse, r, the NF neighbour slabs
+  static __host__ __device__ int stage(int R) { return NF * NP * NP + NP * NP + NP * R + NF * NP * R; }
+  // floats per warp: two stages, the T tile, two mbarriers (as 4 floats)
+  static __host__ __device__ int warp(int R) { return 2 * stage(R) + TcShape<NP, S>::MT * 16 * TcShape<NP, S>::RS + 4; }
+};
+
+// One damped block-Jacobi sweep on the tensor cores (as k_msweep_tc) with each warp's cell
+// data staged by 1-D bulk copies into two shared-memory stages: while the warp computes
+// cell K, the copies of its next cell (the six off-diagonal FP32 blocks, an FP32 inverse,
+// r and the six neighbour iterate slabs of NP x R values) are in flight.  BF16 inverses
+// (not a multiple of 16 bytes per cell) are prefetched by the lanes into registers.  Every
+// wait on a stage is bounded: on a timeout the kernel sets *err, waits (bounded) for its
+// other stage and returns.  Needs NP * NP * 4 and NP * R * 4 to be multiples of 16 bytes.
+template <int NP, int S, typename TI, typename TOUT>
+__global__ void __launch_bounds__(256) k_msweep_tcb(const float* __restrict__ Ac, const TI* __restrict__ D,
+                                                    const int* __restrict__ nbr, int C, int R,
+                                                    const float* __restrict__ r32, const float* __restrict__ zo,
+                                                    TOUT* __restrict__ zn, float om, int first, int x3, int* err) {
+  using Sh = TcShape<NP, S>;
+  constexpr int NF = S - 1, MT = Sh::MT, KS = Sh::KS, RS = Sh::RS, NT = Sh::NT;
+  constexpr bool kBulkD = std::is_same<TI, float>::value;
+  constexpr int DPL = (NP * NP + 31) / 32;   // inverse entries per lane (register prefetch)
+  extern __shared__ float smem_tcb[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
+  const int stg = TcbShape<NP, S>::stage(R);
+  float* base = smem_tcb + (size_t)warp * TcbShape<NP, S>::warp(R);
+  float* stage[2] = {base, base + stg};
+  float* Ts = base + 2 * stg;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(Ts + MT * 16 * RS);   // 16-byte aligned (see warp())
+  const int wpb = blockDim.x >> 5;
+  const int nt_used = (R + 7) >> 3;
+  const int stride = gridDim.x * wpb;
+  const int K0 = blockIdx.x * wpb + warp;
+  if (K0 >= C) return;
+  if (lane == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  // the copies of cell K into stage st (lane 0)
+  auto issue = [&](int st, int K) {
+    float* As = stage[st];
+    float* Ds = As + NF * NP * NP;
+    float* rs = Ds + NP * NP;
+    float* zs = rs + NP * R;
+    const uint32_t slab = (uint32_t)(NP * R * sizeof(float));
+    uint32_t bytes = slab + (kBulkD ? NP * NP * sizeof(float) : 0);
+    int nb[NF];
+    for (int s = 0; s < NF; ++s) {
+      nb[s] = first ? -1 : __ldg(nbr + (size_t)K * NF + s);
+      if (nb[s] >= 0) bytes += slab;
+    }
+    if (!first) bytes += NF * NP * NP * sizeof(float);
+    // order this warp's earlier generic-proxy reads of the stage before the async writes
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(&bar[st], bytes);
+    if (!first) bulk_g2s(As, Ac + ((size_t)K * S + 1) * NP * NP, NF * NP * NP * sizeof(float), &bar[st]);
+    if (kBulkD) bulk_g2s(Ds, reinterpret_cast<const float*>(D) + (size_t)K * NP * NP, NP * NP * sizeof(float), &bar[st]);
+    bulk_g2s(rs, r32 + (size_t)K * NP * R, slab, &bar[st]);
+    for (int s = 0; s < NF; ++s)
+      if (nb[s] >= 0) bulk_g2s(zs + (size_t)s * NP * R, zo + (size_t)nb[s] * NP * R, slab, &bar[st]);
+  };
+  // bounded wait on a stage (lane 0 polls; the result is broadcast)
+  auto wait = [&](int st, uint32_t parity) -> bool {
+    int ok = 1;
+    if (lane == 0) {
+      long long spins = 0;
+      while (!mbar_try_wait(&bar[st], parity)) {
+        if (++spins > (1LL << 24)) { ok = 0; break; }
+      }
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();
+    return ok != 0;
+  };
+  float dreg[DPL];   // BF16 inverse of the next cell, prefetched by the lanes
+  auto load_d = [&](int K) {
+    if (!kBulkD)
+#pragma unroll
+      for (int t = 0; t < DPL; ++t) {
+        const int e = lane + 32 * t;
+        dreg[t] = e < NP * NP ? to_f<TI>(D[(size_t)K * NP * NP + e]) : 0.f;
+      }
+  };
+  if (lane == 0) issue(0, K0);
+  load_d(K0);
+  uint32_t phase[2] = {0u, 0u};
+  bool pending[2] = {true, false};
+  int it = 0;
+  for (int K = K0; K < C; K += stride, ++it) {
+    const int cur = it & 1, nxt = cur ^ 1;
+    const int Kn = K + stride;
+    // this cell's BF16 inverse from the registers into its stage
+    if (!kBulkD) {
+      float* Ds = stage[cur] + NF * NP * NP;
+#pragma unroll
+      for (int t = 0; t < DPL; ++t) {
+        const int e = lane + 32 * t;
+        if (e < NP * NP) Ds[e] = dreg[t];
+      }
+    }
+    __syncwarp();
+    if (Kn < C) {
+      if (lane == 0) issue(nxt, Kn);
+      pending[nxt] = true;
+      load_d(Kn);
+    }
+    if (!wait(cur, phase[cur])) {
+      if (lane == 0) atomicExch(err, 1);
+      if (pending[nxt] && Kn < C) wait(nxt, phase[nxt]);
+      return;
+    }
+    phase[cur] ^= 1u;
+    pending[cur] = false;
+    const float* As = stage[cur];
+    const float* Ds = As + NF * NP * NP;
+    const float* rb = Ds + NP * NP;
+    const float* zsl = rb + NP * R;
+    float c[MT][NT][4];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) {
+        const int row0 = mt * 16 + gid, row1 = row0 + 8, col = nt * 8 + 2 * tig;
+        c[mt][nt][0] = (row0 < NP && col < R) ? rb[row0 * R + col] : 0.f;
+        c[mt][nt][1] = (row0 < NP && col + 1 < R) ? rb[row0 * R + col + 1] : 0.f;
+        c[mt][nt][2] = (row1 < NP && col < R) ? rb[row1 * R + col] : 0.f;
+        c[mt][nt][3] = (row1 < NP && col + 1 < R) ? rb[row1 * R + col + 1] : 0.f;
+      }
+    if (!first) {
+#pragma unroll 1
+      for (int s = 1; s < S; ++s) {
+        const int J = __ldg(nbr + (size_t)K * NF + s - 1);
+        if (J < 0) continue;
+        const float* zb = zsl + (size_t)(s - 1) * NP * R;
+        const float* Ab = As + (s - 1) * NP * NP;
+#pragma unroll
+        for (int kk = 0; kk < KS; ++kk) {
+          const int q0 = kk * 8 + tig, q1 = q0 + 4;
+          uint32_t bh[NT][2], bl[NT][2];
+#pragma unroll
+          for (int nt = 0; nt < NT; ++nt) {
+            const int rr = nt * 8 + gid;
+            const float v0 = (q0 < NP && rr < R) ? zb[q0 * R + rr] : 0.f;
+            const float v1 = (q1 < NP && rr < R) ? zb[q1 * R + rr] : 0.f;
+            tf32_split(v0, bh[nt][0], bl[nt][0]);
+            tf32_split(v1, bh[nt][1], bl[nt][1]);
+          }
+#pragma unroll
+          for (int mt = 0; mt < MT; ++mt) {
+            const int row0 = mt * 16 + gid, row1 = row0 + 8;
+            const float f0 = (row0 < NP && q0 < NP) ? -Ab[row0 * NP + q0] : 0.f;
+            const float f1 = (row1 < NP && q0 < NP) ? -Ab[row1 * NP + q0] : 0.f;
+            const float f2 = (row0 < NP && q1 < NP) ? -Ab[row0 * NP + q1] : 0.f;
+            const float f3 = (row1 < NP && q1 < NP) ? -Ab[row1 * NP + q1] : 0.f;
+            uint32_t ah[4], al[4];
+            tf32_split(f0, ah[0], al[0]);
+            tf32_split(f1, ah[1], al[1]);
+            tf32_split(f2, ah[2], al[2]);
+            tf32_split(f3, ah[3], al[3]);
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+              if (nt >= nt_used) break;
+              if (x3) {
+                mma_tf32(c[mt][nt], al, bh[nt]);
+                mma_tf32(c[mt][nt], ah, bl[nt]);
+              }
+              mma_tf32(c[mt][nt], ah, bh[nt]);
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) {
+        const int row0 = mt * 16 + gid, row1 = row0 + 8, col = nt * 8 + 2 * tig;
+        if (row0 < NP) { Ts[row0 * RS + col] = c[mt][nt][0]; Ts[row0 * RS + col + 1] = c[mt][nt][1]; }
+        if (row1 < NP) { Ts[row1 * RS + col] = c[mt][nt][2]; Ts[row1 * RS + col + 1] = c[mt][nt][3]; }
+      }
+    __syncwarp();
+    float e[MT][NT][4];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) e[mt][nt][k] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < KS; ++kk) {
+      const int q0 = kk * 8 + tig, q1 = q0 + 4;
+      uint32_t bh[NT][2], bl[NT][2];
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) {
+        const int rr = nt * 8 + gid;
+        const float v0 = (q0 < NP) ? Ts[q0 * RS + rr] : 0.f;
+        const float v1 = (q1 < NP) ? Ts[q1 * RS + rr] : 0.f;
+        tf32_split(v0, bh[nt][0], bl[nt][0]);
+        tf32_split(v1, bh[nt][1], bl[nt][1]);
+      }
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt) {
+        const int row0 = mt * 16 + gid, row1 = row0 + 8;
+        const float f0 = (row0 < NP && q0 < NP) ? Ds[row0 * NP + q0] : 0.f;
+        const float f1 = (row1 < NP && q0 < NP) ? Ds[row1 * NP + q0] : 0.f;
+        const float f2 = (row0 < NP && q1 < NP) ? Ds[row0 * NP + q1] : 0.f;
+        const float f3 = (row1 < NP && q1 < NP) ? Ds[row1 * NP + q1] : 0.f;
+        uint32_t ah[4], al[4];
+        tf32_split(f0, ah[0], al[0]);
+        tf32_split(f1, ah[1], al[1]);
+        tf32_split(f2, ah[2], al[2]);
+        tf32_split(f3, ah[3], al[3]);
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          if (nt >= nt_used) break;
+          if (x3) {
+            mma_tf32(e[mt][nt], al, bh[nt]);
+            mma_tf32(e[mt][nt], ah, bl[nt]);
+          }
+          mma_tf32(e[mt][nt], ah, bh[nt]);
+        }
+      }
+    }
+    // zn = (1 - om) zo + om E   (first sweep: om E); zo of cell K is its own iterate
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int row = mt * 16 + gid + ((k >> 1) << 3), col = nt * 8 + 2 * tig + (k & 1);
+          if (row < NP && col < R) {
+            const size_t o = ((size_t)K * NP + row) * R + col;
+            const float v = first ? om * e[mt][nt][k] : fmaf(1.f - om, __ldg(zo + o), om * e[mt][nt][k]);
+            zn[o] = (TOUT)v;
+          }
+        }
+      }
+    __syncwarp();
+  }
+}
+
 }  // namespace
 
 // ====================================================================== host engine
@@ -859,8 +1137,8 @@ struct MLev {
   float *r32 = nullptr, *s0 = nullptr, *s1 = nullptr;
   int lcap = 0;
   MState* st = nullptr;
-  // tuned launch shapes
-  int tc_wpb = 8, tc_grid = 0, sp_wpb = 8, sp_grid = 0;
+  // tuned launch shapes; tc_bulk: the sweep stages each cell by bulk copies (k_msweep_tcb)
+  int tc_wpb = 8, tc_grid = 0, sp_wpb = 8, sp_grid = 0, tc_bulk = 0;
 };
 
 }  // namespace
@@ -884,6 +1162,7 @@ struct MrhsEngine {
   cudaStream_t s = nullptr;
   // autotuner record: per level 0 the chosen shapes and their times
   double tune[16] = {};
+  int* tc_err = nullptr;  // set by the bulk-copy sweep when a copy did not complete in time
 };
 
 namespace {
@@ -961,6 +1240,31 @@ void sweep_tc(MrhsEngine* E, const MLev& L, const TI* D, const float* r32, const
   E->launches++;
 }
 
+// the bulk-copy sweep applies when every staged piece is a multiple of 16 bytes
+bool tcb_ok(const MrhsEngine* E) {
+  const int np = E->v.np;
+  return (np * np * 4) % 16 == 0 && (np * E->R * 4) % 16 == 0;
+}
+
+size_t tcb_smem(int np, int dim, int R, int wpb) {
+  size_t ws = 0;
+  MRHS_ND_SWITCH(np, dim, { ws = TcbShape<NP, 2 * DIM + 1>::warp(R); });
+  return ws * sizeof(float) * wpb;
+}
+
+template <typename TI, typename TOUT>
+void sweep_tcb(MrhsEngine* E, const MLev& L, const TI* D, const float* r32, const float* zo, TOUT* zn,
+               int first, int wpb, int grid) {
+  const size_t sm = tcb_smem(E->v.np, E->v.dim, E->R, wpb);
+  MRHS_ND_SWITCH(E->v.np, E->v.dim, {
+    constexpr int S = 2 * DIM + 1;
+    auto kern = k_msweep_tcb<NP, S, TI, TOUT>;
+    kern<<<grid, wpb * 32, sm, E->s>>>(L.Acm, D, L.nbr, L.C, E->R, r32, zo, zn, (float)E->v.omega, first,
+                                       E->x3 ? 1 : 0, E->tc_err);
+  });
+  E->launches++;
+}
+
 // allow the tensor-core sweeps the device's opt-in shared memory
 void tc_prepare(MrhsEngine* E) {
   int dev = 0, optin = 0;
@@ -972,6 +1276,10 @@ void tc_prepare(MrhsEngine* E) {
     MCK(cudaFuncSetAttribute(k_msweep_tc<NP, S, float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     MCK(cudaFuncSetAttribute(k_msweep_tc<NP, S, __nv_bfloat16, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     MCK(cudaFuncSetAttribute(k_msweep_tc<NP, S, __nv_bfloat16, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    MCK(cudaFuncSetAttribute(k_msweep_tcb<NP, S, float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    MCK(cudaFuncSetAttribute(k_msweep_tcb<NP, S, float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    MCK(cudaFuncSetAttribute(k_msweep_tcb<NP, S, __nv_bfloat16, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    MCK(cudaFuncSetAttribute(k_msweep_tcb<NP, S, __nv_bfloat16, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   });
 }
 
@@ -1031,6 +1339,16 @@ void smooth(MrhsEngine* E, int lev) {
   for (int k = 0; k < sw; ++k) {
     const float* zo = buf[(k + 1) & 1];
     const int grid = L.tc_grid > 0 ? L.tc_grid : grid_for(L.C, L.tc_wpb, 1 << 30);
+    if (L.tc_bulk) {
+      if (k == sw - 1) {
+        if (L.D16) sweep_tcb<__nv_bfloat16, double>(E, L, L.D16, L.r32, zo, L.z, k == 0, L.tc_wpb, grid);
+        else sweep_tcb<float, double>(E, L, L.D32, L.r32, zo, L.z, k == 0, L.tc_wpb, grid);
+      } else {
+        if (L.D16) sweep_tcb<__nv_bfloat16, float>(E, L, L.D16, L.r32, zo, buf[k & 1], k == 0, L.tc_wpb, grid);
+        else sweep_tcb<float, float>(E, L, L.D32, L.r32, zo, buf[k & 1], k == 0, L.tc_wpb, grid);
+      }
+      continue;
+    }
     if (k == sw - 1) {
       if (L.D16) sweep_tc<__nv_bfloat16, double>(E, L, L.D16, L.r32, zo, L.z, k == 0, L.tc_wpb, grid);
       else sweep_tc<float, double>(E, L, L.D32, L.r32, zo, L.z, k == 0, L.tc_wpb, grid);
@@ -1219,6 +1537,10 @@ void autotune(MrhsEngine* E) {
   int dev = 0, smem_optin = 0;
   MCK(cudaGetDevice(&dev));
   MCK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  // KCMG_TC_BULK=1 runs every level's sweep as the bulk-copy pipeline, 0 never (tests,
+  // tuning); unset, the tuner times both and keeps the faster
+  const char* fb = getenv("KCMG_TC_BULK");
+  const int force_bulk = fb ? atoi(fb) : -1;
   for (int lev = 0; lev < E->v.nlev - 1; ++lev) {
     MLev& L = E->lv[lev];
     if (L.C < 256) continue;                        // small levels: defaults
@@ -1253,9 +1575,41 @@ void autotune(MrhsEngine* E) {
         if (ms < bt) { bt = ms; bw = wpb; bg = gmode == 0 ? 0 : grid; }
       }
     }
+    // the bulk-copy pipeline: warps per block, resident grid
+    int bb = 0;
+    if (tcb_ok(E) && force_bulk != 0)
+      for (int wpb : {2, 4, 8}) {
+        const size_t sm = tcb_smem(E->v.np, E->v.dim, E->R, wpb);
+        if ((int)sm > smem_optin) continue;
+        const int per_sm = std::max(1, std::min((int)(smem_optin / sm), 64 / wpb));
+        const int grid = std::min(grid_for(L.C, wpb, 1 << 30), E->nsm * per_sm);
+        const float ms = time_it(E, [&] {
+          if (L.D16) sweep_tcb<__nv_bfloat16, float>(E, L, L.D16, L.r32, L.s0, L.s1, 0, wpb, grid);
+          else sweep_tcb<float, float>(E, L, L.D32, L.r32, L.s0, L.s1, 0, wpb, grid);
+        }, reps);
+        if (ms < bt) { bt = ms; bw = wpb; bg = grid; bb = 1; }
+      }
     L.tc_wpb = bw;
     L.tc_grid = bg;
-    if (lev == 0) { E->tune[2] = bw; E->tune[3] = bg; E->tune[4] = bt; }
+    L.tc_bulk = bb;
+    if (lev == 0) { E->tune[2] = bw; E->tune[3] = bg; E->tune[4] = bt; E->tune[8] = bb; }
+  }
+  if (force_bulk == 1 && E->mixed && tcb_ok(E)) {
+    int wpb = 4;   // the widest block whose stages fit the opt-in shared memory
+    while (wpb > 1 && (int)tcb_smem(E->v.np, E->v.dim, E->R, wpb) > smem_optin) wpb /= 2;
+    const size_t sm = tcb_smem(E->v.np, E->v.dim, E->R, wpb);
+    if ((int)sm <= smem_optin) {
+      const int per_sm = std::max(1, std::min((int)(smem_optin / sm), 16));
+      for (int lev = 0; lev < E->v.nlev - 1; ++lev) {
+        MLev& L = E->lv[lev];
+        L.tc_bulk = 1;
+        L.tc_wpb = wpb;
+        L.tc_grid = std::min(grid_for(L.C, wpb, 1 << 30), E->nsm * per_sm);
+      }
+      E->tune[2] = wpb;
+      E->tune[3] = E->lv[0].tc_grid;
+      E->tune[8] = 1;
+    }
   }
   E->launches = 0;
 }
@@ -1274,6 +1628,8 @@ void build(MrhsEngine* E, const MrhsView& v, int R) {
   const size_t bs = (size_t)np * np;
   E->lv.resize(v.nlev);
   int* fail = malloc_dev<int>(E, 1);
+  E->tc_err = malloc_dev<int>(E, 1);
+  MCK(cudaMemsetAsync(E->tc_err, 0, sizeof(int), E->s));
   double* inv = nullptr;
   for (int l = 0; l < v.nlev; ++l) {
     MLev& L = E->lv[l];
@@ -1458,8 +1814,15 @@ kcmg_status mrhs_solve(MrhsEngine** peng, const MrhsView& v, const double* b, do
     for (int l = 0; l < v.nlev - 1; ++l)
       MCK(cudaMemcpyAsync(&hs[l], E->lv[l].st, sizeof(MState), cudaMemcpyDeviceToHost, E->s));
     MCK(cudaMemcpyAsync(x, L.x, NR * sizeof(double), cudaMemcpyDefault, E->s));
+    int tc_err = 0;
+    MCK(cudaMemcpyAsync(&tc_err, E->tc_err, sizeof(int), cudaMemcpyDeviceToHost, E->s));
     MCK(cudaStreamSynchronize(E->s));
     MCK(cudaGetLastError());
+    if (tc_err) {   // a bulk copy of the tensor-core sweep did not complete within its wait bound
+      MCK(cudaMemsetAsync(E->tc_err, 0, sizeof(int), E->s));
+      if (err) *err = "tensor-core sweep: a bulk copy did not complete in time; the result is invalid";
+      return KCMG_CUDA_ERROR;
+    }
     double worst = 0.0, res0max = 0.0;
     bool all_ok = true, finite = true;
     for (int r = 0; r < R; ++r) {
@@ -1500,9 +1863,9 @@ kcmg_status mrhs_solve(MrhsEngine** peng, const MrhsView& v, const double* b, do
 
 int mrhs_tuning(const MrhsEngine* E, double* out, int nout) {
   if (!E) return 0;
-  const double vals[8] = {E->tune[0], E->tune[1], E->tune[2], E->tune[3], E->tune[4],
-                          (double)E->lv[0].lcap, (double)E->R, E->x3 ? 1.0 : 0.0};
-  const int n = std::min(nout, 8);
+  const double vals[9] = {E->tune[0], E->tune[1], E->tune[2], E->tune[3], E->tune[4],
+                          (double)E->lv[0].lcap, (double)E->R, E->x3 ? 1.0 : 0.0, E->tune[8]};
+  const int n = std::min(nout, 9);
   for (int i = 0; i < n; ++i) out[i] = vals[i];
   return n;
 }

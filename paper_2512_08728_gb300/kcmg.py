@@ -233,10 +233,10 @@ def kcmg_smooth_multi(ctx, level, r):
 
 def kcmg_mrhs_tuning(ctx):
     """Launch shapes the multi-right-hand-side autotuner chose (see kcmg.h)."""
-    out = np.zeros(8)
+    out = np.zeros(9)
     _check(ctx, load_library().kcmg_mrhs_tuning(ctx, out.ctypes.data, out.size))
     keys = ["spmm_warps", "spmm_ms", "sweep_warps", "sweep_grid", "sweep_ms", "lcap0", "nrhs",
-            "x3"]
+            "x3", "sweep_bulk"]
     return dict(zip(keys, out.tolist()))
 
 

@@ -199,3 +199,31 @@ def test_short_restart_length_with_long_task_parallel_cycle(nrhs):
     s.close()
     assert info["status"] in (0, 1), info
     assert info["rel_res"] < 1.0
+
+
+@pytest.mark.parametrize("name", ["sipg3d_p2_8cube", "ragged_3d_p2", "sipg3d_p3_8cube_zstretch"])
+@pytest.mark.parametrize("precision,tol", [("mixed", 2e-5), ("mixed_bf16", 2e-2)])
+@pytest.mark.parametrize("nrhs", [32, 6])
+def test_bulk_copy_tensor_core_sweep_matches_oracle(name, precision, tol, nrhs, monkeypatch):
+    """The tensor-core sweep with every cell's blocks, inverse, residual and neighbour slabs
+    staged by double-buffered 1-D bulk copies (forced on every level), against the oracle."""
+    monkeypatch.setenv("KCMG_TC_BULK", "1")
+    pr = _problem(name)
+    orc = OracleSolver.from_problem(pr)
+    s = pkg.KCycleSolver(pr, precision=precision)
+    rng = np.random.default_rng(8)
+    for lev in range(pr.nlevels - 1):
+        Rm = rng.standard_normal((orc.ndof(lev), nrhs))
+        Z = s.smooth_multi(lev, Rm)
+        ref = np.stack([orc.smooth(lev, Rm[:, j]) for j in range(nrhs)], axis=1)
+        assert _rel(Z, ref) < tol, (lev, _rel(Z, ref))
+    assert s.mrhs_tuning()["sweep_bulk"] == 1.0
+    s.close()
+    # and a whole batched solve on it, column by column against the oracle
+    pm = _problem(name, nrhs=nrhs)
+    s = pkg.KCycleSolver(pm, precision=precision)
+    X, info = s.solve(pm.b, rtol=RTOL_GPU, maxiter=2000)
+    assert s.mrhs_tuning()["sweep_bulk"] == 1.0
+    s.close()
+    assert info["status"] == 0, info
+    _check_columns(pm, X, info)

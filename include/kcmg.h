@@ -130,6 +130,18 @@ typedef struct {
                                 of partition k for the residual b - A x.  omega and sweeps
                                 as above (0.5 and 2 are typical).  Single right-hand side
                                 solves only. */
+    const double *mf_nu;     /* optional, with mf_F: the fine operator is the SIPG operator of
+                                the cell-wise coefficient mf_nu [ncells] whose off-diagonal
+                                blocks are gamma_F F_k^{RL} (slot 1 + 2k) and gamma_F F_k^{LR}
+                                (slot 2 + 2k), gamma_F = 2 nu_K nu_J / (nu_K + nu_J), with mf_F
+                                [dim][4][np][np] the face reference matrices (LL, LR, RL, RR;
+                                the layout of kcmg_grad_lognu).  Setup checks that they
+                                reproduce the given blocks (KCMG_INVALID_ARG otherwise); the
+                                FP32 block-Jacobi sweeps of level 0 then apply the coupling
+                                matrix-free, reading one coefficient per cell instead of six
+                                FP32 blocks.  FP32-smoother forms only (mixed and
+                                iterative-refinement); NULL = stored blocks.  Copied at setup. */
+    const double *mf_F;
 } kcmg_params;
 
 /* Fill p with the defaults of Sec. 4.2 / Alg. BJ for the given sizes (blocks, prolong

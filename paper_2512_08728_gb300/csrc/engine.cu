@@ -36,6 +36,8 @@ struct Level {
   // additive Schwarz smoother (Alg. AS): transposed patch inverses of partitions 0 and 1,
   // patch solutions and the sweep's residual, all in the smoother's precision
   void *as_inv0 = nullptr, *as_inv1 = nullptr, *as_z = nullptr, *as_r = nullptr;
+  // matrix-free level-0 coupling (FP32 sweeps): coefficient per cell, face matrices
+  float *mf_nu = nullptr, *mf_F = nullptr;
   int lcap = 0;
   int nblk = 1;                     // blocks of the multi-column dot kernels
   int nblk2 = 1;                    // blocks of the update / finish / norm kernels
@@ -411,7 +413,15 @@ struct Cycle {
     for (int k = 0; k < sw; ++k) {
       T* out = buf[k & 1];
       const T* old = buf[(k + 1) & 1];
-      if (std::is_same<T, double>::value) {
+      if (!std::is_same<T, double>::value && L.mf_nu) {   // level 0, coupling matrix-free
+        if (L.D16)
+          launch_bj_sweep_mf<__nv_bfloat16>(ctx->np, ctx->dim, L.n, L.mf_nu, L.mf_F, L.D16, L.N, L.rows_pad,
+                                            L.block_rows, (const float*)r, (const float*)old, (float*)out, om,
+                                            k == 0, s);
+        else
+          launch_bj_sweep_mf<float>(ctx->np, ctx->dim, L.n, L.mf_nu, L.mf_F, L.D32, L.N, L.rows_pad,
+                                    L.block_rows, (const float*)r, (const float*)old, (float*)out, om, k == 0, s);
+      } else if (std::is_same<T, double>::value) {
         launch_bj_sweep<double, double>(ctx->np, ctx->dim, (const double*)Ainner(L), L.D64, L.nbr, L.N,
                                         L.G, L.rows_pad, L.block_rows, (const double*)r,
                                         (const double*)old, (double*)out, om, k == 0, s);
@@ -1092,6 +1102,26 @@ kcmg_ctx* build_ctx(const kcmg_params* p, cudaStream_t user, const double* block
     ctx->P32 = dalloc<float>(ctx, ctx->nch * bs);
     launch_convert<double, float>(ctx->P64, ctx->P32, ctx->nch * bs, ctx->s);
     build_hierarchy(ctx, blocks_override ? blocks_override : p->blocks);
+    if (p->mf_nu || p->mf_F) {   // matrix-free level-0 coupling for the FP32 sweeps
+      REQUIRE(p->mf_nu && p->mf_F, "mf_nu and mf_F go together");
+      REQUIRE(ctx->mixed, "the matrix-free level-0 sweeps serve the FP32-smoother forms");
+      REQUIRE(!blocks_override, "matrix-free data describes the forward operator only");
+      Level& L0 = ctx->lv[0];
+      const size_t nF = (size_t)ctx->dim * 4 * ctx->np * ctx->np;
+      double* nu64 = dalloc<double>(ctx, L0.ncell);
+      double* F64 = dalloc<double>(ctx, nF);
+      copy_in(ctx, nu64, p->mf_nu, L0.ncell);
+      copy_in(ctx, F64, p->mf_F, nF);
+      double md = 0, ma = 0;
+      CK(mf_check(ctx->np, ctx->dim, L0.n, nu64, F64, L0.nat, &md, &ma, ctx->s));
+      REQUIRE(md <= 1e-12 * ma, "matrix-free data does not reproduce the off-diagonal blocks "
+              "(max difference %.3e, max entry %.3e)", md, ma);
+      L0.mf_nu = dalloc<float>(ctx, L0.ncell);
+      L0.mf_F = dalloc<float>(ctx, nF);
+      launch_convert<double, float>(nu64, L0.mf_nu, L0.ncell, ctx->s);
+      launch_convert<double, float>(F64, L0.mf_F, nF, ctx->s);
+      CK(cudaGetLastError());
+    }
     // cycle vectors: level 0 basis capacity from lmax (or a default), coarse levels from
     // the per-level iteration caps (3 stored corrections per cycle)
     for (int l = 0; l < ctx->nlev - 1; ++l) {
@@ -1642,6 +1672,12 @@ kcmg_status kcmg_kernel_report(kcmg_ctx* ctx, int reps, double* out, int nout) {
             launch_bj_sweep<double, double>(np, ctx->dim, L.A64, L.D64, L.nbr, L.N, L.G, L.rows_pad, L.block_rows,
                                             static_cast<double*>(L.b), static_cast<double*>(L.t),
                                             static_cast<double*>(L.z), ctx->p.omega, 0, ctx->s);
+          else if (L.mf_nu && L.D16)
+            launch_bj_sweep_mf<__nv_bfloat16>(np, ctx->dim, L.n, L.mf_nu, L.mf_F, L.D16, L.N, L.rows_pad,
+                                              L.block_rows, L.r_lo, L.t_lo, L.z_lo, ctx->p.omega, 0, ctx->s);
+          else if (L.mf_nu)
+            launch_bj_sweep_mf<float>(np, ctx->dim, L.n, L.mf_nu, L.mf_F, L.D32, L.N, L.rows_pad, L.block_rows,
+                                      L.r_lo, L.t_lo, L.z_lo, ctx->p.omega, 0, ctx->s);
           else if (L.D16)
             launch_bj_sweep<float, __nv_bfloat16>(np, ctx->dim, L.A32, L.D16, L.nbr, L.N, L.G, L.rows_pad,
                                                   L.block_rows, L.r_lo, L.t_lo, L.z_lo, ctx->p.omega, 0, ctx->s);
@@ -1653,7 +1689,8 @@ kcmg_status kcmg_kernel_report(kcmg_ctx* ctx, int reps, double* out, int nout) {
         CK(cudaEventSynchronize(e1));
         CK(cudaEventElapsedTime(&ms, e0, e1));
         out[o + 2] = ms / reps;
-        out[o + 3] = (double)(S - 1) * L.N * np * sb + (double)L.N * np * ib + 3.0 * L.N * sb;
+        out[o + 3] = L.mf_nu ? (double)L.ncell * 4 + (double)L.N * np * ib + 3.0 * L.N * sb   // coefficient,
+                             : (double)(S - 1) * L.N * np * sb + (double)L.N * np * ib + 3.0 * L.N * sb;  // inverses, vectors
       };
       time_level(0, 3);
       const int o1 = 7 + KCMG_MAX_LEVELS + kCoarsePhases;

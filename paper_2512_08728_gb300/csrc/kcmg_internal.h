@@ -136,6 +136,14 @@ template <typename T>
 void launch_as_combine(int np, int dim, const int* n, int N, const T* zP, const T* xold, T* xnew,
                        double omega, int first, cudaStream_t s);
 
+// matrix-free coupling of the finest level (matfree.cu)
+template <typename TI>
+void launch_bj_sweep_mf(int np, int dim, const int* n, const float* nu, const float* F, const TI* Dinv, int N,
+                        int rows_pad, int block_rows, const float* r, const float* zold, float* znew,
+                        double omega, int first, cudaStream_t s);
+cudaError_t mf_check(int np, int dim, const int* n, const double* nu, const double* F, const double* nat,
+                     double* maxdiff, double* maxabs, cudaStream_t s);
+
 // setup kernels (FP64, natural layout [S][C][np][np])
 int launch_galerkin(int np, int dim, const double* Af, const int* nbrf, const int* nf,
                     const int* nc, const double* P, double* Ac, cudaStream_t s);

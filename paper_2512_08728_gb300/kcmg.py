@@ -33,7 +33,8 @@ class kcmg_params(C.Structure):
                 ("precision", C.c_int), ("use_graph", C.c_int), ("coarse_persistent", C.c_int),
                 ("tc_tf32_only", C.c_int), ("async_smooth", C.c_int),
                 ("ir_inner_rtol", C.c_double), ("ir_max_steps", C.c_int),
-                ("ir_inner_maxit", C.c_int), ("smoother", C.c_int)]
+                ("ir_inner_maxit", C.c_int), ("smoother", C.c_int),
+                ("mf_nu", C.c_void_p), ("mf_F", C.c_void_p)]
 
 
 class kcmg_info(C.Structure):
@@ -340,7 +341,7 @@ class KCycleSolver:
     def __init__(self, problem, precision="fp64", use_graph=True, omega=0.7, sweeps=5,
                  lmax=0, lvl_rtol=None, lvl_maxit=None, coarse_persistent=True, stream=None,
                  tc_tf32_only=0, async_smooth=0, ir_inner_rtol=None, ir_max_steps=None,
-                 ir_inner_maxit=None, smoother="bj"):
+                 ir_inner_maxit=None, smoother="bj", matrix_free=False):
         pr = problem
         self.dim, self.np_, self.nlevels = pr.d, pr.np_, pr.nlevels
         self.ndof = pr.ndof
@@ -360,6 +361,12 @@ class KCycleSolver:
         if smoother not in ("bj", "as"):
             raise ValueError("smoother must be 'bj' (Alg. BJ) or 'as' (Alg. AS)")
         p.smoother = 1 if smoother == "as" else 0
+        keep = []
+        if matrix_free:   # level-0 FP32 sweeps from the coefficient field and face matrices
+            nu = np.ascontiguousarray(pr.nu, dtype=np.float64)
+            Fm = np.ascontiguousarray(pr.ref["F"], dtype=np.float64)
+            p.mf_nu, p.mf_F = nu.ctypes.data, Fm.ctypes.data
+            keep = [nu, Fm]
         if lvl_rtol is not None:
             for i, v in enumerate(lvl_rtol):
                 p.lvl_rtol[i] = v
@@ -368,6 +375,7 @@ class KCycleSolver:
                 p.lvl_maxit[i] = v
         self.params = p
         self.ctx = kcmg_setup(p, pr.blocks, pr.prolong, stream)
+        del keep
 
     def close(self):
         if getattr(self, "ctx", None):

@@ -4,6 +4,8 @@ Tolerances: FP64 kernels agree with the oracle to rounding (1e-12 relative to th
 entry); FP32 kernels to 1e-5; whole solves reach a true FP64 relative residual <= 1e-10
 and a solution within 1e-8 (relative, 2-norm) of the oracle's solution.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -500,3 +502,47 @@ def test_schwarz_smoother_in_the_refinement_form():
     s.close()
     assert info["status"] == 0, info
     _check_solution(pr, x, info, x_or)
+
+
+# ------------------------------------------------------------------ matrix-free fine coupling
+@pytest.mark.parametrize("name", ["sipg2d_p1_16x16", "sipg3d_p2_8cube", "ragged_3d_p2", "sipg3d_p3_8cube_zstretch"])
+@pytest.mark.parametrize("precision,tol", [("mixed", 3e-5), ("mixed_bf16", 2e-2)])
+def test_matrix_free_fine_sweeps_match_oracle(name, precision, tol):
+    """Level-0 FP32 sweeps with the off-diagonal coupling applied from the coefficient field
+    and the face reference matrices (gamma_F F_k^{RL}, gamma_F F_k^{LR}) instead of stored
+    blocks: against the oracle's Alg. BJ and against the stored-block sweeps."""
+    pr = _problem(name)
+    orc = OracleSolver.from_problem(pr)
+    s_mf = pkg.KCycleSolver(pr, precision=precision, matrix_free=True)
+    s_st = pkg.KCycleSolver(pr, precision=precision)
+    rng = np.random.default_rng(21)
+    for lev in range(pr.nlevels - 1):
+        r = rng.standard_normal(orc.ndof(lev))
+        z_mf, z_st = s_mf.smooth(lev, r), s_st.smooth(lev, r)
+        assert _rel(z_mf, orc.smooth(lev, r)) < tol
+        assert _rel(z_mf, z_st) < (2e-6 if precision == "mixed" else 2e-3)
+    s_mf.close()
+    s_st.close()
+
+
+@pytest.mark.parametrize("name", ["sipg3d_p2_8cube", "ragged_3d_p2", "sipg2d_p1_32x32_5lev"])
+@pytest.mark.parametrize("m", [0, 3])
+def test_matrix_free_fine_sweeps_solve_matches_oracle(name, m):
+    pr = _problem(name)
+    x_or, _ = OracleSolver.from_problem(pr, async_smooth=m).solve(pr.b, rtol=1e-10, maxiter=2000)
+    s = pkg.KCycleSolver(pr, precision="mixed_bf16", matrix_free=True, async_smooth=m)
+    x, info = s.solve(pr.b, rtol=RTOL_GPU, maxiter=2000)
+    s.close()
+    assert info["status"] == 0, info
+    _check_solution(pr, x, info, x_or)
+
+
+def test_matrix_free_setup_rejects_a_coefficient_that_does_not_match():
+    pr = _problem("sipg3d_p2_8cube")
+    shell = dataclasses.replace(pr, nu=pr.nu * np.where(np.arange(pr.ncells) == 5, 1.5, 1.0))
+    with pytest.raises(pkg.KcmgError) as e:
+        pkg.KCycleSolver(shell, precision="mixed", matrix_free=True)
+    assert e.value.status == 5
+    with pytest.raises(pkg.KcmgError) as e:                    # FP64 smoother: not served
+        pkg.KCycleSolver(pr, precision="fp64", matrix_free=True)
+    assert e.value.status == 5

@@ -568,8 +568,10 @@ def main():
     s.close()
 
     # the other forms: one timed solve each, after the solve that captures its graph
-    def time_form(prob, bb, xx, prec, am, smoother, lmax=LMAX, maxiter=None):
+    def time_form(prob, bb, xx, prec, am, smoother, lmax=LMAX, maxiter=None, matrix_free=False):
         skw = dict(smoother="as", omega=AS_OMEGA, sweeps=AS_SWEEPS) if smoother == "as" else {}
+        if matrix_free:
+            skw["matrix_free"] = True
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sm = pkg.KCycleSolver(prob, precision=prec, use_graph=True, lmax=lmax,
@@ -608,7 +610,9 @@ def main():
                       f"+ RM steps per cycle beside it"), "lmax": lmax,
             "smoother": ("Alg. AS: additive Schwarz on two partitions of overlapping 2^d-cell "
                          f"patches, omega {AS_OMEGA}, {AS_SWEEPS} sweeps" if smoother == "as"
-                         else "Alg. BJ: block Jacobi, omega 0.7, 5 sweeps"),
+                         else "Alg. BJ: block Jacobi, omega 0.7, 5 sweeps")
+                        + ("; level-0 coupling matrix-free from the coefficient field and the face "
+                           "reference matrices" if matrix_free else ""),
             "smoother_sweep": {"bound": "hbm" if prec != "fp64" else "alu",
                                "achieved": rp["sweep_bytes"] / (rp["sweep_ms"] * 1e-3) / 1e9,
                                "peak": sw_peak, "unit": "GB/s",
@@ -635,6 +639,9 @@ def main():
             if smoother == "as":
                 fname += "_schwarz"
             forms[fname] = time_form(pr, b, x, prec, am, smoother)
+        # the FP32 sweeps with the level-0 coupling applied matrix-free from the coefficient field
+        forms[f"mixed_bf16_task_parallel_m{HEADLINE_ASYNC_M}_matrix_free"] = time_form(
+            pr, b, x, "mixed_bf16", HEADLINE_ASYNC_M, "bj", matrix_free=True)
         if not args.no_stretched and ws == 1:
             # the mixed-precision configuration: 48^3 cells, p = 3, stretched 1:10 in z, nu
             # 1:1e4 (block Jacobi stalls near 2e-4 on it; the Schwarz smoother converges)

@@ -255,9 +255,16 @@ MRHS_LMAX = 100
 MRHS_PRECISION = "mixed_bf16"
 
 
+# the batched FP32 sweep kernels the autotuner chooses from (kcmg_mrhs_tuning out[8])
+SWEEP_KERNELS = {0: "tensor-core TF32x3 smoother sweeps (FP32 accumulation)",
+                 1: "tensor-core TF32x3 smoother sweeps, bulk-copy staged (FP32 accumulation)",
+                 2: "FP32 CUDA-core smoother sweeps"}
+SWEEP_KERNEL_NAMES = {0: "k_msweep_tc", 1: "k_msweep_tcb", 2: "k_msweep_simt"}
+
+
 def run_mrhs(pkg, rank, dev, stream, hbm_peak, args):
     """The batched form: 32 right-hand sides solved together (one K-cycle per column,
-    shared operator applications, tensor-core sweeps).  value = DOFs x columns / s."""
+    shared operator applications, FP32 sweeps).  value = DOFs x columns / s."""
     import torch
 
     from workloads import workload
@@ -305,8 +312,8 @@ def run_mrhs(pkg, rank, dev, stream, hbm_peak, args):
     C = pm.ndof // pm.np_
     np2, S = pm.np_ * pm.np_, 2 * pm.d + 1
     inv_b = 2 if prec_m == "mixed_bf16" else 4
-    # algorithmic bytes of one tensor-core sweep (sweeps 2..5): FP32 off-diagonal blocks,
-    # stored inverses, r (FP32) and the old and new iterates (FP32), each once
+    # algorithmic bytes of one FP32 sweep (sweeps 2..5): FP32 off-diagonal blocks, stored
+    # inverses, r (FP32) and the old and new iterates (FP32), each once
     sweep_bytes = C * ((S - 1) * np2 * 4 + np2 * inv_b) + 3 * pm.ndof * R * 4
     sweep_gbs = sweep_bytes / (tune["sweep_ms"] * 1e-3) / 1e9 if tune["sweep_ms"] > 0 else 0.0
     # FP64 block SpMM: one FMA per block element and column
@@ -318,14 +325,15 @@ def run_mrhs(pkg, rank, dev, stream, hbm_peak, args):
         "lmax": lmax_m, "precision": prec_m, "kernel_launches": inf["kernel_launches"],
         "level0_cycle": f"Alg. AsyncMG, m = {HEADLINE_ASYNC_M} (every column)",
         "single_column_solves": single,
-        "dtype": ("tensor-core TF32x3 smoother sweeps (FP32 accumulation)"
+        "dtype": (SWEEP_KERNELS.get(int(tune["sweep_kernel"]), "?")
                   + (", BF16 block inverses" if prec_m == "mixed_bf16" else "")
                   + "; f64 residual minimisation, transfers, coarsest solve")
                  if prec_m != "fp64" else "f64",
         "autotuner": tune,
-        "sweep_tc": {"bound": "hbm", "achieved": sweep_gbs, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": sweep_gbs / hbm_peak, "bytes_per_launch": sweep_bytes,
-                     "ms_per_launch": tune["sweep_ms"]},
+        "sweep": {"kernel": SWEEP_KERNEL_NAMES.get(int(tune["sweep_kernel"]), "?"),
+                  "bound": "hbm", "achieved": sweep_gbs, "peak": hbm_peak, "unit": "GB/s",
+                  "frac": sweep_gbs / hbm_peak, "bytes_per_launch": sweep_bytes,
+                  "ms_per_launch": tune["sweep_ms"]},
         "spmm_fp64": {"bound": "alu", "achieved": spmm_tflops, "peak": FP64_TFLOPS,
                       "unit": "TFLOP/s", "frac": spmm_tflops / FP64_TFLOPS,
                       "ms_per_launch": tune["spmm_ms"]},

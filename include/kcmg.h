@@ -279,11 +279,14 @@ kcmg_status kcmg_smooth_multi(kcmg_ctx *ctx, int level, int nrhs, const double *
 
 /* Launch shapes the multi-right-hand-side autotuner chose at the first batched solve of
    ctx: out[0] warps per block of the FP64 block SpMM, out[1] its time (ms), out[2] warps
-   per block of the tensor-core sweep, out[3] its grid (0 = one warp per cell), out[4] its
+   per block of the FP32 sweep, out[3] its grid (0 = one warp per cell), out[4] its
    time (ms), out[5] level-0 basis capacity per column, out[6] nrhs, out[7] 1 if the
-   sweep splits each product into three TF32 products (tc_tf32_only = 0), out[8] 1 if the
-   sweep stages each cell's blocks, inverse, r and neighbour slabs by double-buffered 1-D
-   bulk copies (chosen when it times faster).  Zero-filled up to nout. */
+   tensor-core sweeps split each product into three TF32 products (tc_tf32_only = 0),
+   out[8] the level-0 sweep kernel, the fastest of three: 0 = tensor cores (one warp per
+   cell), 1 = tensor cores with each cell's blocks, inverse, r and neighbour slabs staged
+   by double-buffered 1-D bulk copies, 2 = FP32 CUDA cores (register-blocked; exact FP32
+   products).  The environment variable KCMG_SWEEP = tc | tcb | simt, read at the first
+   batched solve, forces one kernel on every level.  Zero-filled up to nout. */
 kcmg_status kcmg_mrhs_tuning(kcmg_ctx *ctx, double *out, int nout);
 
 /* Level sizes: number of cells of a level (0 if out of range). */

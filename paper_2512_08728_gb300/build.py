@@ -14,7 +14,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libkcmg.so")
 SOURCES = ["kernels.cu", "engine.cu", "coarse_cycle_f64.cu", "coarse_cycle_f32.cu", "coarse_cycle_bf16.cu",
-           "coarse_cycle_ir32.cu", "coarse_cycle_ir32_bf16.cu", "noalloc.cu", "mrhs.cu", "schwarz.cu", "matfree.cu"]
+           "coarse_cycle_ir32.cu", "coarse_cycle_ir32_bf16.cu", "noalloc.cu", "mrhs.cu", "mrhs_simt.cu", "schwarz.cu",
+           "matfree.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

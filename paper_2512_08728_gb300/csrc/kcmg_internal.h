@@ -283,6 +283,17 @@ kcmg_status mrhs_apply(MrhsEngine* eng, int level, const double* x, double* y);
 kcmg_status mrhs_smooth(MrhsEngine* eng, int level, const double* r, double* z);
 // Launch shapes the autotuner chose (out[0..nout)), see kcmg_mrhs_tuning.
 int mrhs_tuning(const MrhsEngine* eng, double* out, int nout);
+
+// The batched FP32 block-Jacobi sweep on the CUDA cores (mrhs_simt.cu): Ac [C][S][np][np]
+// FP32 cell-major blocks, D [C][np][np] inverses, r32 / zo [C np][R] FP32, zn [C np][R];
+// wpb warps per block, grid blocks (resident; each warp walks cell groups).
+size_t msweep_simt_smem(int np, int dim, bool bf16, int wpb);   // dynamic shared memory per block
+int msweep_simt_units(int np, int C);                            // cell groups of a level
+cudaError_t msweep_simt_prepare(int np, int dim, int smem_optin);
+template <typename TI, typename TOUT>
+void launch_msweep_simt(int np, int dim, const float* Ac, const TI* D, const int* nbr, int C, int R,
+                        const float* r32, const float* zo, TOUT* zn, float om, int first, int wpb, int grid,
+                        cudaStream_t s);
 void mrhs_destroy(MrhsEngine* eng);
 
 int block_rows_for(int np);  // threads per block of the operator kernels (whole cells)

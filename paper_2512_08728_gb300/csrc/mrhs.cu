@@ -1114,6 +1114,7 @@ __global__ void __launch_bounds__(256) k_msweep_tcb(const float* __restrict__ Ac
   }
 }
 
+
 }  // namespace
 
 // ====================================================================== host engine
@@ -1137,8 +1138,9 @@ struct MLev {
   float *r32 = nullptr, *s0 = nullptr, *s1 = nullptr;
   int lcap = 0;
   MState* st = nullptr;
-  // tuned launch shapes; tc_bulk: the sweep stages each cell by bulk copies (k_msweep_tcb)
-  int tc_wpb = 8, tc_grid = 0, sp_wpb = 8, sp_grid = 0, tc_bulk = 0;
+  // tuned launch shapes; sweep_kind: the FP32 sweep kernel (0: tensor cores, k_msweep_tc;
+  // 1: tensor cores with bulk-copy staging, k_msweep_tcb; 2: CUDA cores, k_msweep_simt)
+  int tc_wpb = 8, tc_grid = 0, sp_wpb = 8, sp_grid = 0, sweep_kind = 0;
 };
 
 }  // namespace
@@ -1265,6 +1267,21 @@ void sweep_tcb(MrhsEngine* E, const MLev& L, const TI* D, const float* r32, cons
   E->launches++;
 }
 
+template <typename TI, typename TOUT>
+void sweep_simt(MrhsEngine* E, const MLev& L, const TI* D, const float* r32, const float* zo, TOUT* zn,
+                int first, int wpb, int grid) {
+  launch_msweep_simt<TI, TOUT>(E->v.np, E->v.dim, L.Acm, D, L.nbr, L.C, E->R, r32, zo, zn, (float)E->v.omega,
+                               first, wpb, grid, E->s);
+  E->launches++;
+}
+
+// the resident grid of the CUDA-core sweep: blocks per SM from the shared memory per block
+int simt_grid(const MrhsEngine* E, const MLev& L, int wpb, int smem_optin) {
+  const size_t sm = msweep_simt_smem(E->v.np, E->v.dim, L.D16 != nullptr, wpb);
+  const int per_sm = std::max(1, std::min((int)(smem_optin / std::max<size_t>(sm, 1)), 64 / wpb));
+  return std::min(grid_for(msweep_simt_units(E->v.np, L.C), wpb, 1 << 30), E->nsm * per_sm);
+}
+
 // allow the tensor-core sweeps the device's opt-in shared memory
 void tc_prepare(MrhsEngine* E) {
   int dev = 0, optin = 0;
@@ -1281,6 +1298,7 @@ void tc_prepare(MrhsEngine* E) {
     MCK(cudaFuncSetAttribute(k_msweep_tcb<NP, S, __nv_bfloat16, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     MCK(cudaFuncSetAttribute(k_msweep_tcb<NP, S, __nv_bfloat16, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   });
+  MCK(msweep_simt_prepare(E->v.np, E->v.dim, optin));
 }
 
 void sweep64(MrhsEngine* E, const MLev& L, const double* rv, const double* zo, double* zn, int first) {
@@ -1339,7 +1357,17 @@ void smooth(MrhsEngine* E, int lev) {
   for (int k = 0; k < sw; ++k) {
     const float* zo = buf[(k + 1) & 1];
     const int grid = L.tc_grid > 0 ? L.tc_grid : grid_for(L.C, L.tc_wpb, 1 << 30);
-    if (L.tc_bulk) {
+    if (L.sweep_kind == 2) {
+      if (k == sw - 1) {
+        if (L.D16) sweep_simt<__nv_bfloat16, double>(E, L, L.D16, L.r32, zo, L.z, k == 0, L.tc_wpb, grid);
+        else sweep_simt<float, double>(E, L, L.D32, L.r32, zo, L.z, k == 0, L.tc_wpb, grid);
+      } else {
+        if (L.D16) sweep_simt<__nv_bfloat16, float>(E, L, L.D16, L.r32, zo, buf[k & 1], k == 0, L.tc_wpb, grid);
+        else sweep_simt<float, float>(E, L, L.D32, L.r32, zo, buf[k & 1], k == 0, L.tc_wpb, grid);
+      }
+      continue;
+    }
+    if (L.sweep_kind == 1) {
       if (k == sw - 1) {
         if (L.D16) sweep_tcb<__nv_bfloat16, double>(E, L, L.D16, L.r32, zo, L.z, k == 0, L.tc_wpb, grid);
         else sweep_tcb<float, double>(E, L, L.D32, L.r32, zo, L.z, k == 0, L.tc_wpb, grid);
@@ -1530,17 +1558,21 @@ float time_it(MrhsEngine* E, F&& f, int reps) {
   return best;
 }
 
-// Autotuner: for every level with enough cells, time the candidate launch shapes of the
-// smoother sweep (tensor-core form: warps per block x grid) and of the FP64 operator
-// (warps per block) on the level's own buffers and keep the fastest.
+// Autotuner: for every level with enough cells, time the candidate kernels and launch
+// shapes of the FP32 smoother sweep (tensor cores: warps per block x grid; tensor cores
+// with bulk-copy staging and the CUDA-core sweep: warps per block on a resident grid) and
+// of the FP64 operator (warps per block) on the level's own buffers; keep the fastest.
 void autotune(MrhsEngine* E) {
   int dev = 0, smem_optin = 0;
   MCK(cudaGetDevice(&dev));
   MCK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  // KCMG_TC_BULK=1 runs every level's sweep as the bulk-copy pipeline, 0 never (tests,
-  // tuning); unset, the tuner times both and keeps the faster
-  const char* fb = getenv("KCMG_TC_BULK");
-  const int force_bulk = fb ? atoi(fb) : -1;
+  // KCMG_SWEEP = tc | tcb | simt runs every level's FP32 sweep with that kernel (tests,
+  // tuning); unset, the tuner times all three and keeps the fastest
+  const char* fk = getenv("KCMG_SWEEP");
+  int force_kind = -1;
+  if (fk && !strcmp(fk, "tc")) force_kind = 0;
+  else if (fk && !strcmp(fk, "tcb")) force_kind = 1;
+  else if (fk && !strcmp(fk, "simt")) force_kind = 2;
   for (int lev = 0; lev < E->v.nlev - 1; ++lev) {
     MLev& L = E->lv[lev];
     if (L.C < 256) continue;                        // small levels: defaults
@@ -1559,7 +1591,8 @@ void autotune(MrhsEngine* E) {
     if (!E->mixed) continue;
     // tensor-core sweep: warps per block and grid (one warp per cell, or a resident grid)
     float bt = 1e30f;
-    int bw = L.tc_wpb, bg = 0;
+    int bw = L.tc_wpb, bg = 0, bk = 0;
+    if (force_kind <= 0)
     for (int wpb : {2, 4, 8, 16}) {
       size_t sm = L.D16 ? tc_smem<__nv_bfloat16, float>(E->v.np, E->v.dim, wpb)
                         : tc_smem<float, float>(E->v.np, E->v.dim, wpb);
@@ -1576,8 +1609,7 @@ void autotune(MrhsEngine* E) {
       }
     }
     // the bulk-copy pipeline: warps per block, resident grid
-    int bb = 0;
-    if (tcb_ok(E) && force_bulk != 0)
+    if (tcb_ok(E) && (force_kind == -1 || force_kind == 1))
       for (int wpb : {2, 4, 8}) {
         const size_t sm = tcb_smem(E->v.np, E->v.dim, E->R, wpb);
         if ((int)sm > smem_optin) continue;
@@ -1587,28 +1619,43 @@ void autotune(MrhsEngine* E) {
           if (L.D16) sweep_tcb<__nv_bfloat16, float>(E, L, L.D16, L.r32, L.s0, L.s1, 0, wpb, grid);
           else sweep_tcb<float, float>(E, L, L.D32, L.r32, L.s0, L.s1, 0, wpb, grid);
         }, reps);
-        if (ms < bt) { bt = ms; bw = wpb; bg = grid; bb = 1; }
+        if (ms < bt) { bt = ms; bw = wpb; bg = grid; bk = 1; }
+      }
+    // the CUDA-core sweep: warps per block, resident grid
+    if (force_kind == -1 || force_kind == 2)
+      for (int wpb : {2, 4, 8}) {
+        if ((int)msweep_simt_smem(E->v.np, E->v.dim, L.D16 != nullptr, wpb) > smem_optin) continue;
+        const int grid = simt_grid(E, L, wpb, smem_optin);
+        const float ms = time_it(E, [&] {
+          if (L.D16) sweep_simt<__nv_bfloat16, float>(E, L, L.D16, L.r32, L.s0, L.s1, 0, wpb, grid);
+          else sweep_simt<float, float>(E, L, L.D32, L.r32, L.s0, L.s1, 0, wpb, grid);
+        }, reps);
+        if (ms < bt) { bt = ms; bw = wpb; bg = grid; bk = 2; }
       }
     L.tc_wpb = bw;
     L.tc_grid = bg;
-    L.tc_bulk = bb;
-    if (lev == 0) { E->tune[2] = bw; E->tune[3] = bg; E->tune[4] = bt; E->tune[8] = bb; }
+    L.sweep_kind = bk;
+    if (lev == 0) { E->tune[2] = bw; E->tune[3] = bg; E->tune[4] = bt; E->tune[8] = bk; }
   }
-  if (force_bulk == 1 && E->mixed && tcb_ok(E)) {
-    int wpb = 4;   // the widest block whose stages fit the opt-in shared memory
-    while (wpb > 1 && (int)tcb_smem(E->v.np, E->v.dim, E->R, wpb) > smem_optin) wpb /= 2;
-    const size_t sm = tcb_smem(E->v.np, E->v.dim, E->R, wpb);
-    if ((int)sm <= smem_optin) {
-      const int per_sm = std::max(1, std::min((int)(smem_optin / sm), 16));
-      for (int lev = 0; lev < E->v.nlev - 1; ++lev) {
-        MLev& L = E->lv[lev];
-        L.tc_bulk = 1;
-        L.tc_wpb = wpb;
+  // a forced kernel also runs on the small levels the tuner skips
+  if (E->mixed && force_kind >= 1 && (force_kind == 2 || tcb_ok(E))) {
+    for (int lev = 0; lev < E->v.nlev - 1; ++lev) {
+      MLev& L = E->lv[lev];
+      if (L.sweep_kind == force_kind) continue;
+      int wpb = 4;   // the widest block (up to 4 warps) whose stages fit the opt-in shared memory
+      if (force_kind == 1) {
+        while (wpb > 1 && (int)tcb_smem(E->v.np, E->v.dim, E->R, wpb) > smem_optin) wpb /= 2;
+        const size_t sm = tcb_smem(E->v.np, E->v.dim, E->R, wpb);
+        if ((int)sm > smem_optin) continue;
+        const int per_sm = std::max(1, std::min((int)(smem_optin / sm), 16));
         L.tc_grid = std::min(grid_for(L.C, wpb, 1 << 30), E->nsm * per_sm);
+      } else {
+        while (wpb > 1 && (int)msweep_simt_smem(E->v.np, E->v.dim, L.D16 != nullptr, wpb) > smem_optin) wpb /= 2;
+        L.tc_grid = simt_grid(E, L, wpb, smem_optin);
       }
-      E->tune[2] = wpb;
-      E->tune[3] = E->lv[0].tc_grid;
-      E->tune[8] = 1;
+      L.sweep_kind = force_kind;
+      L.tc_wpb = wpb;
+      if (lev == 0) { E->tune[2] = wpb; E->tune[3] = L.tc_grid; E->tune[8] = force_kind; }
     }
   }
   E->launches = 0;

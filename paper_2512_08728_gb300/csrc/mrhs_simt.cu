@@ -1,0 +1,345 @@
+// The batched (multi-right-hand-side) block-Jacobi sweep of Alg. BJ on the FP32 CUDA
+// cores.  Per cell the sweep reads six FP32 10x10 blocks, an inverse and three
+// [Np x R] slabs, and does (S Np^2 R) FMAs: 3.5 FMAs per byte at Np = 10, R = 32, below the
+// FP32 FMA rate per byte of HBM bandwidth, so the sweep is bound by HBM on the CUDA cores
+// and gains nothing from tensor-core products.
+#include "kcmg_internal.h"
+
+#include <type_traits>
+
+namespace kcmg {
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+template <typename TI> __device__ __forceinline__ float to_f(TI v);
+template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// ---- cp.async (16/8/4-byte global -> shared copies), per-warp double buffers
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Shape of the CUDA-core sweep: a group of 32 / CPL lanes owns a cell and each lane CPL
+// consecutive right-hand sides (CPL = 2 up to Np = 10, so a warp takes two cells; 1 at
+// Np = 20).  Per cell, shared memory holds the NF off-diagonal FP32 blocks (AB bytes) and
+// the stored inverse (DB bytes, TI), each padded to 16 bytes; a warp has two stages.
+template <int NP, int S, typename TI> struct SimtShape {
+  static constexpr int NF = S - 1;
+  static constexpr int CPL = NP <= 10 ? 2 : 1;
+  static constexpr int CPW = CPL;                                  // cells per warp
+  static constexpr int LPC = 32 / CPL;                             // lanes per cell
+  static constexpr int ASZ = NF * NP * NP * 4;
+  static constexpr int DSZ = NP * NP * (int)sizeof(TI);
+  static constexpr int AB = (ASZ + 15) / 16 * 16;
+  static constexpr int DB = (DSZ + 15) / 16 * 16;
+  static constexpr int CS = AB + DB;                               // bytes per cell
+  static constexpr int WB = 2 * CPW * CS;                          // bytes per warp
+  // copy granules: each divides its piece's size and every source offset (the blocks of
+  // cell K start at (K S + 1) NP^2 floats, the inverse at K NP^2 entries)
+  static constexpr int AG = (NP * NP * 4) % 16 == 0 ? 16 : (NP * NP * 4) % 8 == 0 ? 8 : 4;
+  static constexpr int DG = DSZ % 16 == 0 ? 16 : DSZ % 8 == 0 ? 8 : DSZ % 4 == 0 ? 4 : 0;
+};
+
+template <int G> __device__ __forceinline__ void cp_async_g(void* dst, const void* src) {
+  if (G == 16) cp_async16(dst, src);
+  else if (G == 8) cp_async8(dst, src);
+  else cp_async4(dst, src);
+}
+
+// Two consecutive FP32 values (PAIR: one 8-byte access; the offset is even) or one.
+template <int CPL, bool PAIR>
+__device__ __forceinline__ void ld_cols(const float* p, int c0, int R, float* v) {
+  if (CPL == 2 && PAIR) {
+    if (c0 < R) {
+      const float2 t = __ldg(reinterpret_cast<const float2*>(p + c0));
+      v[0] = t.x;
+      v[1] = t.y;
+    } else {
+      v[0] = v[1] = 0.f;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) v[c] = c0 + c < R ? __ldg(p + c0 + c) : 0.f;
+  }
+}
+template <int CPL, bool PAIR>
+__device__ __forceinline__ void st_cols(float* p, int c0, int R, const float* v) {
+  if (CPL == 2 && PAIR) {
+    if (c0 < R) *reinterpret_cast<float2*>(p + c0) = make_float2(v[0], v[1]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < CPL; ++c)
+      if (c0 + c < R) p[c0 + c] = v[c];
+  }
+}
+template <int CPL, bool PAIR>
+__device__ __forceinline__ void st_cols(double* p, int c0, int R, const float* v) {
+  if (CPL == 2 && PAIR) {
+    if (c0 < R) *reinterpret_cast<double2*>(p + c0) = make_double2(v[0], v[1]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < CPL; ++c)
+      if (c0 + c < R) p[c0 + c] = v[c];
+  }
+}
+
+// two consecutive stored-inverse entries (NP even: 8-byte FP32 / 4-byte BF16 aligned)
+template <typename TI> __device__ __forceinline__ float2 ld_pair(const TI* p);
+template <> __device__ __forceinline__ float2 ld_pair<float>(const float* p) {
+  return *reinterpret_cast<const float2*>(p);
+}
+template <> __device__ __forceinline__ float2 ld_pair<__nv_bfloat16>(const __nv_bfloat16* p) {
+  return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+}
+
+// One damped block-Jacobi sweep (Alg. BJ) for R right-hand sides on the FP32 CUDA cores:
+//   T = r_K - sum_s A_{K,s} zo_{nbr(K,s)},   zn_K = (1 - om) zo_K + om D_K^{-1} T
+// (first sweep: zn_K = om D_K^{-1} r_K).  Each lane keeps its CPL columns of T for all NP
+// rows in registers; the block rows come from shared memory as 8-byte broadcasts (one per
+// two FMAs per column), the neighbour slabs from L2 with one 8-byte load per row.  Every
+// warp walks its own sequence of cell groups with two cp.async stages: the blocks and
+// inverse of its next group are in flight while it computes the current one.
+// Ac: [C][S][NP][NP] FP32 (cell-major, slot 0 unused here), D: [C][NP][NP] (TI);
+// r32, zo: [C*NP][R] FP32; zn: [C*NP][R] (TOUT).  PAIR: R even.
+template <int NP, int S, typename TI, typename TOUT, bool PAIR>
+__global__ void __launch_bounds__(256) k_msweep_simt(const float* __restrict__ Ac, const TI* __restrict__ D,
+                                                     const int* __restrict__ nbr, int C, int R,
+                                                     const float* __restrict__ r32, const float* __restrict__ zo,
+                                                     TOUT* __restrict__ zn, float om, int first) {
+  using Sh = SimtShape<NP, S, TI>;
+  constexpr int NF = Sh::NF, CPL = Sh::CPL, CPW = Sh::CPW, LPC = Sh::LPC;
+  constexpr bool EVEN = NP % 2 == 0;
+  extern __shared__ __align__(16) unsigned char smem_simt[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  unsigned char* wbase = smem_simt + (size_t)warp * Sh::WB;
+  const int nunits = (C + CPW - 1) / CPW;
+  const int nw = gridDim.x * wpb;
+  int u = blockIdx.x * wpb + warp;
+  if (u >= nunits) return;
+  const int hl = lane / LPC, h = lane - hl * LPC;   // cell of the group, lane within it
+  const int c0 = h * CPL;                           // first column of this lane
+
+  // the copies of group un into stage st (all lanes; cells past C are skipped)
+  auto load_unit = [&](int un, int st) {
+    unsigned char* dst = wbase + (size_t)st * CPW * Sh::CS;
+#pragma unroll
+    for (int c = 0; c < CPW; ++c) {
+      const int K = un * CPW + c;
+      if (K >= C) break;
+      unsigned char* cd = dst + c * Sh::CS;
+      if (!first) {
+        const unsigned char* src = reinterpret_cast<const unsigned char*>(Ac + ((size_t)K * S + 1) * NP * NP);
+        for (int q = lane; q < Sh::ASZ / Sh::AG; q += 32) cp_async_g<Sh::AG>(cd + q * Sh::AG, src + q * Sh::AG);
+      }
+      const TI* dsrc = D + (size_t)K * NP * NP;
+      if (Sh::DG > 0) {
+        const unsigned char* src = reinterpret_cast<const unsigned char*>(dsrc);
+        for (int q = lane; q < Sh::DSZ / (Sh::DG > 0 ? Sh::DG : 1); q += 32)
+          cp_async_g<(Sh::DG > 0 ? Sh::DG : 4)>(cd + Sh::AB + q * Sh::DG, src + q * Sh::DG);
+      } else {
+        TI* dd = reinterpret_cast<TI*>(cd + Sh::AB);
+        for (int q = lane; q < NP * NP; q += 32) dd[q] = dsrc[q];
+      }
+    }
+  };
+
+  load_unit(u, 0);
+  cp_async_commit();
+  for (int it = 0; u < nunits; u += nw, ++it) {
+    const int st = it & 1;
+    const int un = u + nw;
+    if (un < nunits) load_unit(un, st ^ 1);
+    cp_async_commit();
+    cp_async_wait<1>();   // this lane's copies of stage st have landed
+    __syncwarp();         // ... and every lane's
+    const int K = u * CPW + hl;
+    if (K < C) {
+      const unsigned char* cb = wbase + ((size_t)st * CPW + hl) * Sh::CS;
+      const float* As = reinterpret_cast<const float*>(cb);
+      const TI* Ds = reinterpret_cast<const TI*>(cb + Sh::AB);
+      float t[NP][CPL];
+#pragma unroll
+      for (int i = 0; i < NP; ++i) ld_cols<CPL, PAIR>(r32 + ((size_t)K * NP + i) * R, c0, R, t[i]);
+      if (!first) {
+        int nb[NF];
+#pragma unroll
+        for (int s = 0; s < NF; ++s) nb[s] = __ldg(nbr + (size_t)K * NF + s);
+        float xc[NP][CPL], xn[NP][CPL];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+          if (nb[0] >= 0) ld_cols<CPL, PAIR>(zo + ((size_t)nb[0] * NP + j) * R, c0, R, xc[j]);
+          else
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) xc[j][c] = 0.f;
+        }
+#pragma unroll
+        for (int s = 0; s < NF; ++s) {
+          if (s + 1 < NF) {   // the next neighbour's slab is in flight during this block
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+              if (nb[s + 1] >= 0) ld_cols<CPL, PAIR>(zo + ((size_t)nb[s + 1] * NP + j) * R, c0, R, xn[j]);
+              else
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) xn[j][c] = 0.f;
+            }
+          }
+          const float* Ab = As + s * NP * NP;
+#pragma unroll
+          for (int i = 0; i < NP; ++i) {
+            if (EVEN) {
+#pragma unroll
+              for (int j = 0; j < NP; j += 2) {
+                const float2 a = *reinterpret_cast<const float2*>(Ab + i * NP + j);
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) {
+                  t[i][c] = fmaf(-a.x, xc[j][c], t[i][c]);
+                  t[i][c] = fmaf(-a.y, xc[j + 1][c], t[i][c]);
+                }
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < NP; ++j) {
+                const float a = Ab[i * NP + j];
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) t[i][c] = fmaf(-a, xc[j][c], t[i][c]);
+              }
+            }
+          }
+          if (s + 1 < NF)
+#pragma unroll
+            for (int j = 0; j < NP; ++j)
+#pragma unroll
+              for (int c = 0; c < CPL; ++c) xc[j][c] = xn[j][c];
+        }
+      }
+      // zn = (1 - om) zo + om D^{-1} T
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        float e[CPL];
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) e[c] = 0.f;
+        if (EVEN) {
+#pragma unroll
+          for (int j = 0; j < NP; j += 2) {
+            const float2 d = ld_pair<TI>(Ds + i * NP + j);
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) {
+              e[c] = fmaf(d.x, t[j][c], e[c]);
+              e[c] = fmaf(d.y, t[j + 1][c], e[c]);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < NP; ++j) {
+            const float d = to_f<TI>(Ds[i * NP + j]);
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) e[c] = fmaf(d, t[j][c], e[c]);
+          }
+        }
+        const size_t o = ((size_t)K * NP + i) * R;
+        if (!first) {
+          float zv[CPL];
+          ld_cols<CPL, PAIR>(zo + o, c0, R, zv);
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) e[c] = fmaf(1.f - om, zv[c], om * e[c]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) e[c] = om * e[c];
+        }
+        st_cols<CPL, PAIR>(zn + o, c0, R, e);
+      }
+    }
+    __syncwarp();   // every lane is done with stage st before the next group refills it
+  }
+  cp_async_wait<0>();
+}
+
+template <typename F>
+bool simt_dispatch(int np, int dim, F&& f) {
+  switch (np * 10 + dim) {
+    case 32: f(std::integral_constant<int, 3>{}, std::integral_constant<int, 5>{}); return true;
+    case 62: f(std::integral_constant<int, 6>{}, std::integral_constant<int, 5>{}); return true;
+    case 102: f(std::integral_constant<int, 10>{}, std::integral_constant<int, 5>{}); return true;
+    case 43: f(std::integral_constant<int, 4>{}, std::integral_constant<int, 7>{}); return true;
+    case 103: f(std::integral_constant<int, 10>{}, std::integral_constant<int, 7>{}); return true;
+    case 203: f(std::integral_constant<int, 20>{}, std::integral_constant<int, 7>{}); return true;
+    default: return false;
+  }
+}
+
+}  // namespace
+
+size_t msweep_simt_smem(int np, int dim, bool bf16, int wpb) {
+  size_t wb = 0;
+  simt_dispatch(np, dim, [&](auto NPc, auto Sc) {
+    constexpr int NP = decltype(NPc)::value, S = decltype(Sc)::value;
+    wb = bf16 ? SimtShape<NP, S, __nv_bfloat16>::WB : SimtShape<NP, S, float>::WB;
+  });
+  return wb * wpb;
+}
+
+int msweep_simt_units(int np, int C) { return np <= 10 ? (C + 1) / 2 : C; }
+
+cudaError_t msweep_simt_prepare(int np, int dim, int smem_optin) {
+  cudaError_t err = cudaSuccess;
+  auto set = [&](const void* f) {
+    const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+    if (e != cudaSuccess) err = e;
+  };
+  const bool ok = simt_dispatch(np, dim, [&](auto NPc, auto Sc) {
+    constexpr int NP = decltype(NPc)::value, S = decltype(Sc)::value;
+    set((const void*)k_msweep_simt<NP, S, float, float, true>);
+    set((const void*)k_msweep_simt<NP, S, float, double, true>);
+    set((const void*)k_msweep_simt<NP, S, __nv_bfloat16, float, true>);
+    set((const void*)k_msweep_simt<NP, S, __nv_bfloat16, double, true>);
+    set((const void*)k_msweep_simt<NP, S, float, float, false>);
+    set((const void*)k_msweep_simt<NP, S, float, double, false>);
+    set((const void*)k_msweep_simt<NP, S, __nv_bfloat16, float, false>);
+    set((const void*)k_msweep_simt<NP, S, __nv_bfloat16, double, false>);
+  });
+  return ok ? err : cudaErrorInvalidValue;
+}
+
+template <typename TI, typename TOUT>
+void launch_msweep_simt(int np, int dim, const float* Ac, const TI* D, const int* nbr, int C, int R,
+                        const float* r32, const float* zo, TOUT* zn, float om, int first, int wpb, int grid,
+                        cudaStream_t s) {
+  const size_t sm = msweep_simt_smem(np, dim, std::is_same<TI, __nv_bfloat16>::value, wpb);
+  simt_dispatch(np, dim, [&](auto NPc, auto Sc) {
+    constexpr int NP = decltype(NPc)::value, S = decltype(Sc)::value;
+    if (R % 2 == 0)
+      k_msweep_simt<NP, S, TI, TOUT, true><<<grid, wpb * 32, sm, s>>>(Ac, D, nbr, C, R, r32, zo, zn, om, first);
+    else
+      k_msweep_simt<NP, S, TI, TOUT, false><<<grid, wpb * 32, sm, s>>>(Ac, D, nbr, C, R, r32, zo, zn, om, first);
+  });
+}
+
+template void launch_msweep_simt<float, float>(int, int, const float*, const float*, const int*, int, int,
+                                               const float*, const float*, float*, float, int, int, int,
+                                               cudaStream_t);
+template void launch_msweep_simt<float, double>(int, int, const float*, const float*, const int*, int, int,
+                                                const float*, const float*, double*, float, int, int, int,
+                                                cudaStream_t);
+template void launch_msweep_simt<__nv_bfloat16, float>(int, int, const float*, const __nv_bfloat16*, const int*,
+                                                       int, int, const float*, const float*, float*, float, int,
+                                                       int, int, cudaStream_t);
+template void launch_msweep_simt<__nv_bfloat16, double>(int, int, const float*, const __nv_bfloat16*, const int*,
+                                                        int, int, const float*, const float*, double*, float, int,
+                                                        int, int, cudaStream_t);
+
+}  // namespace kcmg

@@ -237,7 +237,7 @@ def kcmg_mrhs_tuning(ctx):
     out = np.zeros(9)
     _check(ctx, load_library().kcmg_mrhs_tuning(ctx, out.ctypes.data, out.size))
     keys = ["spmm_warps", "spmm_ms", "sweep_warps", "sweep_grid", "sweep_ms", "lcap0", "nrhs",
-            "x3", "sweep_bulk"]
+            "x3", "sweep_kernel"]
     return dict(zip(keys, out.tolist()))
 
 

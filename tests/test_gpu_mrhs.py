@@ -201,13 +201,7 @@ def test_short_restart_length_with_long_task_parallel_cycle(nrhs):
     assert info["rel_res"] < 1.0
 
 
-@pytest.mark.parametrize("name", ["sipg3d_p2_8cube", "ragged_3d_p2", "sipg3d_p3_8cube_zstretch"])
-@pytest.mark.parametrize("precision,tol", [("mixed", 2e-5), ("mixed_bf16", 2e-2)])
-@pytest.mark.parametrize("nrhs", [32, 6])
-def test_bulk_copy_tensor_core_sweep_matches_oracle(name, precision, tol, nrhs, monkeypatch):
-    """The tensor-core sweep with every cell's blocks, inverse, residual and neighbour slabs
-    staged by double-buffered 1-D bulk copies (forced on every level), against the oracle."""
-    monkeypatch.setenv("KCMG_TC_BULK", "1")
+def _forced_sweep_check(name, precision, tol, nrhs, kind, solve):
     pr = _problem(name)
     orc = OracleSolver.from_problem(pr)
     s = pkg.KCycleSolver(pr, precision=precision)
@@ -217,13 +211,38 @@ def test_bulk_copy_tensor_core_sweep_matches_oracle(name, precision, tol, nrhs, 
         Z = s.smooth_multi(lev, Rm)
         ref = np.stack([orc.smooth(lev, Rm[:, j]) for j in range(nrhs)], axis=1)
         assert _rel(Z, ref) < tol, (lev, _rel(Z, ref))
-    assert s.mrhs_tuning()["sweep_bulk"] == 1.0
+    assert s.mrhs_tuning()["sweep_kernel"] == kind
     s.close()
+    if not solve:
+        return
     # and a whole batched solve on it, column by column against the oracle
     pm = _problem(name, nrhs=nrhs)
     s = pkg.KCycleSolver(pm, precision=precision)
     X, info = s.solve(pm.b, rtol=RTOL_GPU, maxiter=2000)
-    assert s.mrhs_tuning()["sweep_bulk"] == 1.0
+    assert s.mrhs_tuning()["sweep_kernel"] == kind
     s.close()
     assert info["status"] == 0, info
     _check_columns(pm, X, info)
+
+
+@pytest.mark.parametrize("name", ["sipg3d_p2_8cube", "ragged_3d_p2", "sipg3d_p3_8cube_zstretch"])
+@pytest.mark.parametrize("precision,tol", [("mixed", 2e-5), ("mixed_bf16", 2e-2)])
+@pytest.mark.parametrize("nrhs", [32, 6])
+def test_bulk_copy_tensor_core_sweep_matches_oracle(name, precision, tol, nrhs, monkeypatch):
+    """The tensor-core sweep with every cell's blocks, inverse, residual and neighbour slabs
+    staged by double-buffered 1-D bulk copies (forced on every level), against the oracle."""
+    monkeypatch.setenv("KCMG_SWEEP", "tcb")
+    _forced_sweep_check(name, precision, tol, nrhs, 1.0, solve=True)
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("precision,tol", [("mixed", 2e-5), ("mixed_bf16", 2e-2)])
+@pytest.mark.parametrize("nrhs", [32, 5])
+def test_cuda_core_sweep_matches_oracle(name, precision, tol, nrhs, monkeypatch):
+    """The register-blocked FP32 sweep on the CUDA cores (forced on every level): every Np of
+    the workloads (3, 4, 6, 10, 20: odd Np reads the blocks one entry at a time, Np = 20
+    gives a warp one cell), an odd column count (one column at a time) and 32, against the
+    oracle's FP64 sweeps; a batched solve on the 3-D p = 2 cases."""
+    monkeypatch.setenv("KCMG_SWEEP", "simt")
+    _forced_sweep_check(name, precision, tol, nrhs, 2.0,
+                        solve=name in ("sipg3d_p2_8cube", "ragged_3d_p2"))

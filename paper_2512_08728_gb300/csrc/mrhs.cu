@@ -1275,11 +1275,11 @@ void sweep_simt(MrhsEngine* E, const MLev& L, const TI* D, const float* r32, con
   E->launches++;
 }
 
-// the resident grid of the CUDA-core sweep: blocks per SM from the shared memory per block
-int simt_grid(const MrhsEngine* E, const MLev& L, int wpb, int smem_optin) {
-  const size_t sm = msweep_simt_smem(E->v.np, E->v.dim, L.D16 != nullptr, wpb);
-  const int per_sm = std::max(1, std::min((int)(smem_optin / std::max<size_t>(sm, 1)), 64 / wpb));
-  return std::min(grid_for(msweep_simt_units(E->v.np, L.C), wpb, 1 << 30), E->nsm * per_sm);
+// the resident grid of the CUDA-core sweep (blocks per SM from the occupancy of the
+// instantiation: registers and shared memory), so that every warp starts at once
+int simt_grid(const MrhsEngine* E, const MLev& L, int wpb) {
+  const int per_sm = msweep_simt_blocks_per_sm(E->v.np, E->v.dim, L.D16 != nullptr, E->R, wpb);
+  return std::min(grid_for(msweep_simt_units(E->v.np, E->R, L.C), wpb, 1 << 30), E->nsm * per_sm);
 }
 
 // allow the tensor-core sweeps the device's opt-in shared memory
@@ -1623,9 +1623,9 @@ void autotune(MrhsEngine* E) {
       }
     // the CUDA-core sweep: warps per block, resident grid
     if (force_kind == -1 || force_kind == 2)
-      for (int wpb : {2, 4, 8}) {
-        if ((int)msweep_simt_smem(E->v.np, E->v.dim, L.D16 != nullptr, wpb) > smem_optin) continue;
-        const int grid = simt_grid(E, L, wpb, smem_optin);
+      for (int wpb : {1, 2, 4, 8}) {
+        if ((int)msweep_simt_smem(E->v.np, E->v.dim, L.D16 != nullptr, E->R, wpb) > smem_optin) continue;
+        const int grid = simt_grid(E, L, wpb);
         const float ms = time_it(E, [&] {
           if (L.D16) sweep_simt<__nv_bfloat16, float>(E, L, L.D16, L.r32, L.s0, L.s1, 0, wpb, grid);
           else sweep_simt<float, float>(E, L, L.D32, L.r32, L.s0, L.s1, 0, wpb, grid);
@@ -1650,8 +1650,8 @@ void autotune(MrhsEngine* E) {
         const int per_sm = std::max(1, std::min((int)(smem_optin / sm), 16));
         L.tc_grid = std::min(grid_for(L.C, wpb, 1 << 30), E->nsm * per_sm);
       } else {
-        while (wpb > 1 && (int)msweep_simt_smem(E->v.np, E->v.dim, L.D16 != nullptr, wpb) > smem_optin) wpb /= 2;
-        L.tc_grid = simt_grid(E, L, wpb, smem_optin);
+        while (wpb > 1 && (int)msweep_simt_smem(E->v.np, E->v.dim, L.D16 != nullptr, E->R, wpb) > smem_optin) wpb /= 2;
+        L.tc_grid = simt_grid(E, L, wpb);
       }
       L.sweep_kind = force_kind;
       L.tc_wpb = wpb;

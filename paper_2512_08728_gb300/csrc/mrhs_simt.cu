@@ -5,6 +5,7 @@
 // and gains nothing from tensor-core products.
 #include "kcmg_internal.h"
 
+#include <algorithm>
 #include <type_traits>
 
 namespace kcmg {
@@ -33,13 +34,13 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Shape of the CUDA-core sweep: a group of 32 / CPL lanes owns a cell and each lane CPL
-// consecutive right-hand sides (CPL = 2 up to Np = 10, so a warp takes two cells; 1 at
-// Np = 20).  Per cell, shared memory holds the NF off-diagonal FP32 blocks (AB bytes) and
-// the stored inverse (DB bytes, TI), each padded to 16 bytes; a warp has two stages.
-template <int NP, int S, typename TI> struct SimtShape {
+// Shape of the CUDA-core sweep: each lane takes CPL consecutive right-hand sides, so
+// 32 / CPL lanes own a cell and a warp takes CPL cells (CPL = 4 for 32 columns, 2 for
+// other column counts, 1 at Np = 20).  Per cell, shared memory holds the NF off-diagonal
+// FP32 blocks (AB bytes) and the stored inverse (DB bytes, TI), each padded to 16 bytes;
+// a warp has two stages.
+template <int NP, int S, typename TI, int CPL> struct SimtShape {
   static constexpr int NF = S - 1;
-  static constexpr int CPL = NP <= 10 ? 2 : 1;
   static constexpr int CPW = CPL;                                  // cells per warp
   static constexpr int LPC = 32 / CPL;                             // lanes per cell
   static constexpr int ASZ = NF * NP * NP * 4;
@@ -60,42 +61,52 @@ template <int G> __device__ __forceinline__ void cp_async_g(void* dst, const voi
   else cp_async4(dst, src);
 }
 
-// Two consecutive FP32 values (PAIR: one 8-byte access; the offset is even) or one.
-template <int CPL, bool PAIR>
-__device__ __forceinline__ void ld_cols(const float* p, int c0, int R, float* v) {
-  if (CPL == 2 && PAIR) {
-    if (c0 < R) {
-      const float2 t = __ldg(reinterpret_cast<const float2*>(p + c0));
-      v[0] = t.x;
-      v[1] = t.y;
+// CPL consecutive columns c0.. of one row: with VEC (R a multiple of CPL, so the offset is
+// too) one CPL*4-byte access, else one column at a time; columns >= R read as zero and
+// are not written.
+template <int CPL, bool VEC> struct Cols {
+  static __device__ __forceinline__ void ld(const float* p, int c0, int R, float* v) {
+    if (VEC && CPL > 1) {
+      if (c0 < R) {
+        if (CPL == 4) {
+          const float4 t = __ldg(reinterpret_cast<const float4*>(p + c0));
+          v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+        } else {
+          const float2 t = __ldg(reinterpret_cast<const float2*>(p + c0));
+          v[0] = t.x; v[1] = t.y;
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) v[c] = 0.f;
+      }
     } else {
-      v[0] = v[1] = 0.f;
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) v[c] = c0 + c < R ? __ldg(p + c0 + c) : 0.f;
     }
-  } else {
-#pragma unroll
-    for (int c = 0; c < CPL; ++c) v[c] = c0 + c < R ? __ldg(p + c0 + c) : 0.f;
   }
-}
-template <int CPL, bool PAIR>
-__device__ __forceinline__ void st_cols(float* p, int c0, int R, const float* v) {
-  if (CPL == 2 && PAIR) {
-    if (c0 < R) *reinterpret_cast<float2*>(p + c0) = make_float2(v[0], v[1]);
-  } else {
+  static __device__ __forceinline__ void st(float* p, int c0, int R, const float* v) {
+    if (VEC && CPL > 1) {
+      if (c0 >= R) return;
+      if (CPL == 4) *reinterpret_cast<float4*>(p + c0) = make_float4(v[0], v[1], v[2], v[3]);
+      else *reinterpret_cast<float2*>(p + c0) = make_float2(v[0], v[1]);
+    } else {
 #pragma unroll
-    for (int c = 0; c < CPL; ++c)
-      if (c0 + c < R) p[c0 + c] = v[c];
+      for (int c = 0; c < CPL; ++c)
+        if (c0 + c < R) p[c0 + c] = v[c];
+    }
   }
-}
-template <int CPL, bool PAIR>
-__device__ __forceinline__ void st_cols(double* p, int c0, int R, const float* v) {
-  if (CPL == 2 && PAIR) {
-    if (c0 < R) *reinterpret_cast<double2*>(p + c0) = make_double2(v[0], v[1]);
-  } else {
+  static __device__ __forceinline__ void st(double* p, int c0, int R, const float* v) {
+    if (VEC && CPL > 1) {
+      if (c0 >= R) return;
 #pragma unroll
-    for (int c = 0; c < CPL; ++c)
-      if (c0 + c < R) p[c0 + c] = v[c];
+      for (int c = 0; c < CPL; c += 2) *reinterpret_cast<double2*>(p + c0 + c) = make_double2(v[c], v[c + 1]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < CPL; ++c)
+        if (c0 + c < R) p[c0 + c] = v[c];
+    }
   }
-}
+};
 
 // two consecutive stored-inverse entries (NP even: 8-byte FP32 / 4-byte BF16 aligned)
 template <typename TI> __device__ __forceinline__ float2 ld_pair(const TI* p);
@@ -109,20 +120,24 @@ template <> __device__ __forceinline__ float2 ld_pair<__nv_bfloat16>(const __nv_
 // One damped block-Jacobi sweep (Alg. BJ) for R right-hand sides on the FP32 CUDA cores:
 //   T = r_K - sum_s A_{K,s} zo_{nbr(K,s)},   zn_K = (1 - om) zo_K + om D_K^{-1} T
 // (first sweep: zn_K = om D_K^{-1} r_K).  Each lane keeps its CPL columns of T for all NP
-// rows in registers; the block rows come from shared memory as 8-byte broadcasts (one per
-// two FMAs per column), the neighbour slabs from L2 with one 8-byte load per row.  Every
-// warp walks its own sequence of cell groups with two cp.async stages: the blocks and
-// inverse of its next group are in flight while it computes the current one.
+// rows in registers.  The block rows come from shared memory as broadcasts (one 8- or
+// 16-byte read per 2-4 FMAs per column), the neighbour slabs from L2 with one read per
+// row; the next neighbour's slab is in flight while a block is applied.  Every warp walks
+// its own sequence of cell groups with two cp.async stages: the blocks and inverse of its
+// next group are in flight while it computes the current one, and the next group's
+// neighbour indices are read one group ahead.
 // Ac: [C][S][NP][NP] FP32 (cell-major, slot 0 unused here), D: [C][NP][NP] (TI);
-// r32, zo: [C*NP][R] FP32; zn: [C*NP][R] (TOUT).  PAIR: R even.
-template <int NP, int S, typename TI, typename TOUT, bool PAIR>
+// r32, zo: [C*NP][R] FP32; zn: [C*NP][R] (TOUT).  RC > 0: R == RC at compile time.
+template <int NP, int S, typename TI, typename TOUT, int CPL, int RC, bool VEC>
 __global__ void __launch_bounds__(256) k_msweep_simt(const float* __restrict__ Ac, const TI* __restrict__ D,
-                                                     const int* __restrict__ nbr, int C, int R,
+                                                     const int* __restrict__ nbr, int C, int Rrt,
                                                      const float* __restrict__ r32, const float* __restrict__ zo,
                                                      TOUT* __restrict__ zn, float om, int first) {
-  using Sh = SimtShape<NP, S, TI>;
-  constexpr int NF = Sh::NF, CPL = Sh::CPL, CPW = Sh::CPW, LPC = Sh::LPC;
+  using Sh = SimtShape<NP, S, TI, CPL>;
+  using Cl = Cols<CPL, VEC>;
+  constexpr int NF = Sh::NF, CPW = Sh::CPW, LPC = Sh::LPC;
   constexpr bool EVEN = NP % 2 == 0;
+  const int R = RC > 0 ? RC : Rrt;
   extern __shared__ __align__(16) unsigned char smem_simt[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
@@ -157,7 +172,29 @@ __global__ void __launch_bounds__(256) k_msweep_simt(const float* __restrict__ A
       }
     }
   };
+  // neighbour indices of this lane's cell in group un (-1: none, or no such cell)
+  auto load_nb = [&](int un, int* nb) {
+    const int K = un * CPW + hl;
+    const bool ok = !first && un < nunits && K < C;
+#pragma unroll
+    for (int s = 0; s < NF; ++s) nb[s] = ok ? __ldg(nbr + (size_t)K * NF + s) : -1;
+  };
+  // this lane's columns of the NP rows of cell J's iterate (zeros for J < 0)
+  auto load_slab = [&](int J, float (*x)[CPL]) {
+    if (J >= 0) {
+      const float* p = zo + (size_t)J * NP * R;
+#pragma unroll
+      for (int j = 0; j < NP; ++j) Cl::ld(p + (size_t)j * R, c0, R, x[j]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < NP; ++j)
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) x[j][c] = 0.f;
+    }
+  };
 
+  int nbc[NF], nbn[NF];
+  load_nb(u, nbc);
   load_unit(u, 0);
   cp_async_commit();
   for (int it = 0; u < nunits; u += nw, ++it) {
@@ -165,58 +202,47 @@ __global__ void __launch_bounds__(256) k_msweep_simt(const float* __restrict__ A
     const int un = u + nw;
     if (un < nunits) load_unit(un, st ^ 1);
     cp_async_commit();
+    load_nb(un, nbn);
+    const int K = u * CPW + hl;
+    const bool act = K < C;
+    float t[NP][CPL], xc[NP][CPL];
+    if (act) {
+#pragma unroll
+      for (int i = 0; i < NP; ++i) Cl::ld(r32 + ((size_t)K * NP + i) * R, c0, R, t[i]);
+      if (!first) load_slab(nbc[0], xc);
+    }
     cp_async_wait<1>();   // this lane's copies of stage st have landed
     __syncwarp();         // ... and every lane's
-    const int K = u * CPW + hl;
-    if (K < C) {
+    if (act) {
       const unsigned char* cb = wbase + ((size_t)st * CPW + hl) * Sh::CS;
       const float* As = reinterpret_cast<const float*>(cb);
       const TI* Ds = reinterpret_cast<const TI*>(cb + Sh::AB);
-      float t[NP][CPL];
-#pragma unroll
-      for (int i = 0; i < NP; ++i) ld_cols<CPL, PAIR>(r32 + ((size_t)K * NP + i) * R, c0, R, t[i]);
       if (!first) {
-        int nb[NF];
-#pragma unroll
-        for (int s = 0; s < NF; ++s) nb[s] = __ldg(nbr + (size_t)K * NF + s);
-        float xc[NP][CPL], xn[NP][CPL];
-#pragma unroll
-        for (int j = 0; j < NP; ++j) {
-          if (nb[0] >= 0) ld_cols<CPL, PAIR>(zo + ((size_t)nb[0] * NP + j) * R, c0, R, xc[j]);
-          else
-#pragma unroll
-            for (int c = 0; c < CPL; ++c) xc[j][c] = 0.f;
-        }
+        float xn[NP][CPL];
 #pragma unroll
         for (int s = 0; s < NF; ++s) {
-          if (s + 1 < NF) {   // the next neighbour's slab is in flight during this block
+          if (s + 1 < NF) load_slab(nbc[s + 1], xn);   // in flight while block s is applied
+          if (nbc[s] >= 0) {
+            const float* Ab = As + s * NP * NP;
 #pragma unroll
-            for (int j = 0; j < NP; ++j) {
-              if (nb[s + 1] >= 0) ld_cols<CPL, PAIR>(zo + ((size_t)nb[s + 1] * NP + j) * R, c0, R, xn[j]);
-              else
+            for (int i = 0; i < NP; ++i) {
+              if (EVEN) {
 #pragma unroll
-                for (int c = 0; c < CPL; ++c) xn[j][c] = 0.f;
-            }
-          }
-          const float* Ab = As + s * NP * NP;
+                for (int j = 0; j < NP; j += 2) {
+                  const float2 a = *reinterpret_cast<const float2*>(Ab + i * NP + j);
 #pragma unroll
-          for (int i = 0; i < NP; ++i) {
-            if (EVEN) {
-#pragma unroll
-              for (int j = 0; j < NP; j += 2) {
-                const float2 a = *reinterpret_cast<const float2*>(Ab + i * NP + j);
-#pragma unroll
-                for (int c = 0; c < CPL; ++c) {
-                  t[i][c] = fmaf(-a.x, xc[j][c], t[i][c]);
-                  t[i][c] = fmaf(-a.y, xc[j + 1][c], t[i][c]);
+                  for (int c = 0; c < CPL; ++c) {
+                    t[i][c] = fmaf(-a.x, xc[j][c], t[i][c]);
+                    t[i][c] = fmaf(-a.y, xc[j + 1][c], t[i][c]);
+                  }
                 }
-              }
-            } else {
+              } else {
 #pragma unroll
-              for (int j = 0; j < NP; ++j) {
-                const float a = Ab[i * NP + j];
+                for (int j = 0; j < NP; ++j) {
+                  const float a = Ab[i * NP + j];
 #pragma unroll
-                for (int c = 0; c < CPL; ++c) t[i][c] = fmaf(-a, xc[j][c], t[i][c]);
+                  for (int c = 0; c < CPL; ++c) t[i][c] = fmaf(-a, xc[j][c], t[i][c]);
+                }
               }
             }
           }
@@ -254,20 +280,26 @@ __global__ void __launch_bounds__(256) k_msweep_simt(const float* __restrict__ A
         const size_t o = ((size_t)K * NP + i) * R;
         if (!first) {
           float zv[CPL];
-          ld_cols<CPL, PAIR>(zo + o, c0, R, zv);
+          Cl::ld(zo + o, c0, R, zv);
 #pragma unroll
           for (int c = 0; c < CPL; ++c) e[c] = fmaf(1.f - om, zv[c], om * e[c]);
         } else {
 #pragma unroll
           for (int c = 0; c < CPL; ++c) e[c] = om * e[c];
         }
-        st_cols<CPL, PAIR>(zn + o, c0, R, e);
+        Cl::st(zn + o, c0, R, e);
       }
     }
+#pragma unroll
+    for (int s = 0; s < NF; ++s) nbc[s] = nbn[s];
     __syncwarp();   // every lane is done with stage st before the next group refills it
   }
   cp_async_wait<0>();
 }
+
+// column blocking of a launch: CPL = 4 with R = 32 (vector accesses), 1 at Np = 20
+// (register budget), else 2
+int simt_cpl(int np, int R) { return np > 10 ? 1 : R == 32 ? 4 : 2; }
 
 template <typename F>
 bool simt_dispatch(int np, int dim, F&& f) {
@@ -284,48 +316,109 @@ bool simt_dispatch(int np, int dim, F&& f) {
 
 }  // namespace
 
-size_t msweep_simt_smem(int np, int dim, bool bf16, int wpb) {
+size_t msweep_simt_smem(int np, int dim, bool bf16, int R, int wpb) {
   size_t wb = 0;
+  const int cpl = simt_cpl(np, R);
   simt_dispatch(np, dim, [&](auto NPc, auto Sc) {
     constexpr int NP = decltype(NPc)::value, S = decltype(Sc)::value;
-    wb = bf16 ? SimtShape<NP, S, __nv_bfloat16>::WB : SimtShape<NP, S, float>::WB;
+    if (cpl == 4) wb = bf16 ? SimtShape<NP, S, __nv_bfloat16, 4>::WB : SimtShape<NP, S, float, 4>::WB;
+    else if (cpl == 2) wb = bf16 ? SimtShape<NP, S, __nv_bfloat16, 2>::WB : SimtShape<NP, S, float, 2>::WB;
+    else wb = bf16 ? SimtShape<NP, S, __nv_bfloat16, 1>::WB : SimtShape<NP, S, float, 1>::WB;
   });
   return wb * wpb;
 }
 
-int msweep_simt_units(int np, int C) { return np <= 10 ? (C + 1) / 2 : C; }
+int msweep_simt_units(int np, int R, int C) {
+  const int cpw = simt_cpl(np, R);
+  return (C + cpw - 1) / cpw;
+}
+
+namespace {
+
+// every instantiation a launch can pick for (NP, S, TI, TOUT): f(kernel pointer)
+template <int NP, int S, typename TI, typename TOUT, typename F>
+void simt_each(F&& f) {
+  if constexpr (NP > 10) {
+    f(k_msweep_simt<NP, S, TI, TOUT, 1, 0, false>);
+  } else {
+    f(k_msweep_simt<NP, S, TI, TOUT, 4, 32, true>);
+    f(k_msweep_simt<NP, S, TI, TOUT, 2, 0, true>);
+    f(k_msweep_simt<NP, S, TI, TOUT, 2, 0, false>);
+  }
+}
+
+}  // namespace
 
 cudaError_t msweep_simt_prepare(int np, int dim, int smem_optin) {
   cudaError_t err = cudaSuccess;
-  auto set = [&](const void* f) {
-    const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+  auto set = [&](auto kern) {
+    const cudaError_t e =
+        cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
     if (e != cudaSuccess) err = e;
   };
   const bool ok = simt_dispatch(np, dim, [&](auto NPc, auto Sc) {
     constexpr int NP = decltype(NPc)::value, S = decltype(Sc)::value;
-    set((const void*)k_msweep_simt<NP, S, float, float, true>);
-    set((const void*)k_msweep_simt<NP, S, float, double, true>);
-    set((const void*)k_msweep_simt<NP, S, __nv_bfloat16, float, true>);
-    set((const void*)k_msweep_simt<NP, S, __nv_bfloat16, double, true>);
-    set((const void*)k_msweep_simt<NP, S, float, float, false>);
-    set((const void*)k_msweep_simt<NP, S, float, double, false>);
-    set((const void*)k_msweep_simt<NP, S, __nv_bfloat16, float, false>);
-    set((const void*)k_msweep_simt<NP, S, __nv_bfloat16, double, false>);
+    simt_each<NP, S, float, float>(set);
+    simt_each<NP, S, float, double>(set);
+    simt_each<NP, S, __nv_bfloat16, float>(set);
+    simt_each<NP, S, __nv_bfloat16, double>(set);
   });
   return ok ? err : cudaErrorInvalidValue;
+}
+
+int msweep_simt_blocks_per_sm(int np, int dim, bool bf16, int R, int wpb) {
+  const size_t sm = msweep_simt_smem(np, dim, bf16, R, wpb);
+  const int cpl = simt_cpl(np, R);
+  int best = 1 << 30;
+  auto occ = [&](auto kern) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, wpb * 32, sm) != cudaSuccess) b = 1;
+    best = std::min(best, b);
+  };
+  // the smaller of the FP32- and FP64-output instantiations the level's sweeps launch
+  simt_dispatch(np, dim, [&](auto NPc, auto Sc) {
+    constexpr int NP = decltype(NPc)::value, S = decltype(Sc)::value;
+    auto both = [&](auto ti) {
+      using TI = decltype(ti);
+      if constexpr (NP > 10) {
+        occ(k_msweep_simt<NP, S, TI, float, 1, 0, false>);
+        occ(k_msweep_simt<NP, S, TI, double, 1, 0, false>);
+      } else {
+        if (cpl == 4) {
+          occ(k_msweep_simt<NP, S, TI, float, 4, 32, true>);
+          occ(k_msweep_simt<NP, S, TI, double, 4, 32, true>);
+        } else {
+          occ(k_msweep_simt<NP, S, TI, float, 2, 0, true>);
+          occ(k_msweep_simt<NP, S, TI, double, 2, 0, true>);
+          occ(k_msweep_simt<NP, S, TI, float, 2, 0, false>);
+          occ(k_msweep_simt<NP, S, TI, double, 2, 0, false>);
+        }
+      }
+    };
+    if (bf16) both(__nv_bfloat16{});
+    else both(float{});
+  });
+  return best == (1 << 30) ? 1 : std::max(best, 1);
 }
 
 template <typename TI, typename TOUT>
 void launch_msweep_simt(int np, int dim, const float* Ac, const TI* D, const int* nbr, int C, int R,
                         const float* r32, const float* zo, TOUT* zn, float om, int first, int wpb, int grid,
                         cudaStream_t s) {
-  const size_t sm = msweep_simt_smem(np, dim, std::is_same<TI, __nv_bfloat16>::value, wpb);
+  const size_t sm = msweep_simt_smem(np, dim, std::is_same<TI, __nv_bfloat16>::value, R, wpb);
+  const int cpl = simt_cpl(np, R);
   simt_dispatch(np, dim, [&](auto NPc, auto Sc) {
     constexpr int NP = decltype(NPc)::value, S = decltype(Sc)::value;
-    if (R % 2 == 0)
-      k_msweep_simt<NP, S, TI, TOUT, true><<<grid, wpb * 32, sm, s>>>(Ac, D, nbr, C, R, r32, zo, zn, om, first);
-    else
-      k_msweep_simt<NP, S, TI, TOUT, false><<<grid, wpb * 32, sm, s>>>(Ac, D, nbr, C, R, r32, zo, zn, om, first);
+    if constexpr (NP > 10) {
+      k_msweep_simt<NP, S, TI, TOUT, 1, 0, false><<<grid, wpb * 32, sm, s>>>(Ac, D, nbr, C, R, r32, zo, zn, om, first);
+    } else {
+      if (cpl == 4)
+        k_msweep_simt<NP, S, TI, TOUT, 4, 32, true><<<grid, wpb * 32, sm, s>>>(Ac, D, nbr, C, R, r32, zo, zn, om, first);
+      else if (R % 2 == 0)
+        k_msweep_simt<NP, S, TI, TOUT, 2, 0, true><<<grid, wpb * 32, sm, s>>>(Ac, D, nbr, C, R, r32, zo, zn, om, first);
+      else
+        k_msweep_simt<NP, S, TI, TOUT, 2, 0, false><<<grid, wpb * 32, sm, s>>>(Ac, D, nbr, C, R, r32, zo, zn, om, first);
+    }
   });
 }
 

@@ -306,7 +306,8 @@ def run_mrhs(pkg, rank, dev, stream, hbm_peak, args):
             ts.append((e0.elapsed_time(e1), ij["iters"]))
         s1.close()
         single[prec] = {"value": pm.ndof * len(ts) / (sum(t for t, _ in ts) * 1e-3), "unit": UNIT,
-                        "cycles": [c for _, c in ts]}
+                        "cycles": [c for _, c in ts],
+                        "dof_cycles_per_s": pm.ndof * sum(c for _, c in ts) / (sum(t for t, _ in ts) * 1e-3)}
     sm.close()
     R = int(pm.b.shape[1])
     C = pm.ndof // pm.np_
@@ -320,6 +321,9 @@ def run_mrhs(pkg, rank, dev, stream, hbm_peak, args):
     spmm_tflops = 2.0 * S * np2 * C * R / (tune["spmm_ms"] * 1e-3) / 1e12 if tune["spmm_ms"] > 0 else 0.0
     return {
         "value": pm.ndof * R / (mms * 1e-3), "unit": UNIT, "workload": wname, "nrhs": R,
+        # DOF-cycles per second (columns x DOFs x level-0 cycles / s): comparable with the
+        # single-column solves when --maxiter bounds both
+        "dof_cycles_per_s": pm.ndof * R * inf["iters"] / (mms * 1e-3),
         "ms_per_step": mms, "status": inf["status"], "rel_res": inf["rel_res"],
         "cycles": inf["iters"], "level_iters": inf["level_iters"][:pm.nlevels],
         "lmax": lmax_m, "precision": prec_m, "kernel_launches": inf["kernel_launches"],

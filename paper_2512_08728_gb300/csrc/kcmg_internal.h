@@ -289,7 +289,7 @@ int mrhs_tuning(const MrhsEngine* eng, double* out, int nout);
 // wpb warps per block, grid blocks (resident; each warp walks cell groups).
 size_t msweep_simt_smem(int np, int dim, bool bf16, int R, int wpb);   // dynamic shared memory per block
 int msweep_simt_units(int np, int R, int C);                            // cell groups of a level
-int msweep_simt_blocks_per_sm(int np, int dim, bool bf16, int R, int wpb);   // resident blocks per SM
+int msweep_simt_blocks_per_sm(int np, int dim, bool bf16, int R, int wpb, bool out64);   // resident blocks per SM
 cudaError_t msweep_simt_prepare(int np, int dim, int smem_optin);
 template <typename TI, typename TOUT>
 void launch_msweep_simt(int np, int dim, const float* Ac, const TI* D, const int* nbr, int C, int R,

@@ -1141,6 +1141,7 @@ struct MLev {
   // tuned launch shapes; sweep_kind: the FP32 sweep kernel (0: tensor cores, k_msweep_tc;
   // 1: tensor cores with bulk-copy staging, k_msweep_tcb; 2: CUDA cores, k_msweep_simt)
   int tc_wpb = 8, tc_grid = 0, sp_wpb = 8, sp_grid = 0, sweep_kind = 0;
+  int tc_grid64 = 0;   // CUDA-core sweep: resident grid of its FP64-output form (last sweep)
 };
 
 }  // namespace
@@ -1277,8 +1278,8 @@ void sweep_simt(MrhsEngine* E, const MLev& L, const TI* D, const float* r32, con
 
 // the resident grid of the CUDA-core sweep (blocks per SM from the occupancy of the
 // instantiation: registers and shared memory), so that every warp starts at once
-int simt_grid(const MrhsEngine* E, const MLev& L, int wpb) {
-  const int per_sm = msweep_simt_blocks_per_sm(E->v.np, E->v.dim, L.D16 != nullptr, E->R, wpb);
+int simt_grid(const MrhsEngine* E, const MLev& L, int wpb, bool out64 = false) {
+  const int per_sm = msweep_simt_blocks_per_sm(E->v.np, E->v.dim, L.D16 != nullptr, E->R, wpb, out64);
   return std::min(grid_for(msweep_simt_units(E->v.np, E->R, L.C), wpb, 1 << 30), E->nsm * per_sm);
 }
 
@@ -1359,8 +1360,9 @@ void smooth(MrhsEngine* E, int lev) {
     const int grid = L.tc_grid > 0 ? L.tc_grid : grid_for(L.C, L.tc_wpb, 1 << 30);
     if (L.sweep_kind == 2) {
       if (k == sw - 1) {
-        if (L.D16) sweep_simt<__nv_bfloat16, double>(E, L, L.D16, L.r32, zo, L.z, k == 0, L.tc_wpb, grid);
-        else sweep_simt<float, double>(E, L, L.D32, L.r32, zo, L.z, k == 0, L.tc_wpb, grid);
+        const int g64 = L.tc_grid64 > 0 ? L.tc_grid64 : grid;
+        if (L.D16) sweep_simt<__nv_bfloat16, double>(E, L, L.D16, L.r32, zo, L.z, k == 0, L.tc_wpb, g64);
+        else sweep_simt<float, double>(E, L, L.D32, L.r32, zo, L.z, k == 0, L.tc_wpb, g64);
       } else {
         if (L.D16) sweep_simt<__nv_bfloat16, float>(E, L, L.D16, L.r32, zo, buf[k & 1], k == 0, L.tc_wpb, grid);
         else sweep_simt<float, float>(E, L, L.D32, L.r32, zo, buf[k & 1], k == 0, L.tc_wpb, grid);
@@ -1635,6 +1637,7 @@ void autotune(MrhsEngine* E) {
     L.tc_wpb = bw;
     L.tc_grid = bg;
     L.sweep_kind = bk;
+    L.tc_grid64 = bk == 2 ? simt_grid(E, L, bw, true) : 0;
     if (lev == 0) { E->tune[2] = bw; E->tune[3] = bg; E->tune[4] = bt; E->tune[8] = bk; }
   }
   // a forced kernel also runs on the small levels the tuner skips
@@ -1652,6 +1655,7 @@ void autotune(MrhsEngine* E) {
       } else {
         while (wpb > 1 && (int)msweep_simt_smem(E->v.np, E->v.dim, L.D16 != nullptr, E->R, wpb) > smem_optin) wpb /= 2;
         L.tc_grid = simt_grid(E, L, wpb);
+        L.tc_grid64 = simt_grid(E, L, wpb, true);
       }
       L.sweep_kind = force_kind;
       L.tc_wpb = wpb;

@@ -121,10 +121,10 @@ template <> __device__ __forceinline__ float2 ld_pair<__nv_bfloat16>(const __nv_
 //   T = r_K - sum_s A_{K,s} zo_{nbr(K,s)},   zn_K = (1 - om) zo_K + om D_K^{-1} T
 // (first sweep: zn_K = om D_K^{-1} r_K).  Each lane keeps its CPL columns of T for all NP
 // rows in registers.  The block rows come from shared memory as broadcasts (one 8- or
-// 16-byte read per 2-4 FMAs per column), the neighbour slabs from L2 with one read per
-// row; the next neighbour's slab is in flight while a block is applied.  Every warp walks
-// its own sequence of cell groups with two cp.async stages: the blocks and inverse of its
-// next group are in flight while it computes the current one, and the next group's
+// 16-byte read per 2-4 FMAs per column), the neighbour slabs, r and zo_K from L2 or HBM
+// with one read per row, each in flight during the phase before its use.  Every warp
+// walks its own sequence of cell groups with two cp.async stages: the blocks and inverse
+// of its next group are in flight while it computes the current one, and the next group's
 // neighbour indices are read one group ahead.
 // Ac: [C][S][NP][NP] FP32 (cell-major, slot 0 unused here), D: [C][NP][NP] (TI);
 // r32, zo: [C*NP][R] FP32; zn: [C*NP][R] (TOUT).  RC > 0: R == RC at compile time.
@@ -193,10 +193,16 @@ __global__ void __launch_bounds__(256) k_msweep_simt(const float* __restrict__ A
     }
   };
 
+  // Register buffers: t (T), xc (the slab being applied), xn (the next load in flight).
+  // Per group the loads are slab 0 .. slab NF-1, then r, then the own iterate zo_K: each is
+  // issued one phase before its use (slab s+1 during block s, r during the last block, zo_K
+  // while r is added, the next group's slab 0 during the inverse product).
   int nbc[NF], nbn[NF];
+  float xc[NP][CPL], xn[NP][CPL];
   load_nb(u, nbc);
   load_unit(u, 0);
   cp_async_commit();
+  if (!first) load_slab(nbc[0], xc);
   for (int it = 0; u < nunits; u += nw, ++it) {
     const int st = it & 1;
     const int un = u + nw;
@@ -205,54 +211,65 @@ __global__ void __launch_bounds__(256) k_msweep_simt(const float* __restrict__ A
     load_nb(un, nbn);
     const int K = u * CPW + hl;
     const bool act = K < C;
-    float t[NP][CPL], xc[NP][CPL];
-    if (act) {
+    float t[NP][CPL];
+    if (first && act)
 #pragma unroll
       for (int i = 0; i < NP; ++i) Cl::ld(r32 + ((size_t)K * NP + i) * R, c0, R, t[i]);
-      if (!first) load_slab(nbc[0], xc);
-    }
     cp_async_wait<1>();   // this lane's copies of stage st have landed
     __syncwarp();         // ... and every lane's
-    if (act) {
-      const unsigned char* cb = wbase + ((size_t)st * CPW + hl) * Sh::CS;
-      const float* As = reinterpret_cast<const float*>(cb);
-      const TI* Ds = reinterpret_cast<const TI*>(cb + Sh::AB);
-      if (!first) {
-        float xn[NP][CPL];
+    const unsigned char* cb = wbase + ((size_t)st * CPW + hl) * Sh::CS;
+    const float* As = reinterpret_cast<const float*>(cb);
+    const TI* Ds = reinterpret_cast<const TI*>(cb + Sh::AB);
+    if (!first && act) {
 #pragma unroll
-        for (int s = 0; s < NF; ++s) {
-          if (s + 1 < NF) load_slab(nbc[s + 1], xn);   // in flight while block s is applied
-          if (nbc[s] >= 0) {
-            const float* Ab = As + s * NP * NP;
+      for (int i = 0; i < NP; ++i)
 #pragma unroll
-            for (int i = 0; i < NP; ++i) {
-              if (EVEN) {
+        for (int c = 0; c < CPL; ++c) t[i][c] = 0.f;
 #pragma unroll
-                for (int j = 0; j < NP; j += 2) {
-                  const float2 a = *reinterpret_cast<const float2*>(Ab + i * NP + j);
+      for (int s = 0; s < NF; ++s) {
+        if (s + 1 < NF) load_slab(nbc[s + 1], xn);
+        else
 #pragma unroll
-                  for (int c = 0; c < CPL; ++c) {
-                    t[i][c] = fmaf(-a.x, xc[j][c], t[i][c]);
-                    t[i][c] = fmaf(-a.y, xc[j + 1][c], t[i][c]);
-                  }
+          for (int i = 0; i < NP; ++i) Cl::ld(r32 + ((size_t)K * NP + i) * R, c0, R, xn[i]);
+        if (nbc[s] >= 0) {
+          const float* Ab = As + s * NP * NP;
+#pragma unroll
+          for (int i = 0; i < NP; ++i) {
+            if (EVEN) {
+#pragma unroll
+              for (int j = 0; j < NP; j += 2) {
+                const float2 a = *reinterpret_cast<const float2*>(Ab + i * NP + j);
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) {
+                  t[i][c] = fmaf(-a.x, xc[j][c], t[i][c]);
+                  t[i][c] = fmaf(-a.y, xc[j + 1][c], t[i][c]);
                 }
-              } else {
+              }
+            } else {
 #pragma unroll
-                for (int j = 0; j < NP; ++j) {
-                  const float a = Ab[i * NP + j];
+              for (int j = 0; j < NP; ++j) {
+                const float a = Ab[i * NP + j];
 #pragma unroll
-                  for (int c = 0; c < CPL; ++c) t[i][c] = fmaf(-a, xc[j][c], t[i][c]);
-                }
+                for (int c = 0; c < CPL; ++c) t[i][c] = fmaf(-a, xc[j][c], t[i][c]);
               }
             }
           }
-          if (s + 1 < NF)
-#pragma unroll
-            for (int j = 0; j < NP; ++j)
-#pragma unroll
-              for (int c = 0; c < CPL; ++c) xc[j][c] = xn[j][c];
         }
+#pragma unroll
+        for (int j = 0; j < NP; ++j)
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) xc[j][c] = xn[j][c];
       }
+      // xc = r: T = r - sum_s A_s x_s; then xc = zo_K for the damping
+#pragma unroll
+      for (int i = 0; i < NP; ++i)
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) t[i][c] += xc[i][c];
+#pragma unroll
+      for (int i = 0; i < NP; ++i) Cl::ld(zo + ((size_t)K * NP + i) * R, c0, R, xc[i]);
+    }
+    if (!first) load_slab(nbn[0], xn);   // the next group's first slab
+    if (act) {
       // zn = (1 - om) zo + om D^{-1} T
 #pragma unroll
       for (int i = 0; i < NP; ++i) {
@@ -277,19 +294,21 @@ __global__ void __launch_bounds__(256) k_msweep_simt(const float* __restrict__ A
             for (int c = 0; c < CPL; ++c) e[c] = fmaf(d, t[j][c], e[c]);
           }
         }
-        const size_t o = ((size_t)K * NP + i) * R;
         if (!first) {
-          float zv[CPL];
-          Cl::ld(zo + o, c0, R, zv);
 #pragma unroll
-          for (int c = 0; c < CPL; ++c) e[c] = fmaf(1.f - om, zv[c], om * e[c]);
+          for (int c = 0; c < CPL; ++c) e[c] = fmaf(1.f - om, xc[i][c], om * e[c]);
         } else {
 #pragma unroll
           for (int c = 0; c < CPL; ++c) e[c] = om * e[c];
         }
-        Cl::st(zn + o, c0, R, e);
+        Cl::st(zn + ((size_t)K * NP + i) * R, c0, R, e);
       }
     }
+    if (!first)
+#pragma unroll
+      for (int j = 0; j < NP; ++j)
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) xc[j][c] = xn[j][c];
 #pragma unroll
     for (int s = 0; s < NF; ++s) nbc[s] = nbn[s];
     __syncwarp();   // every lane is done with stage st before the next group refills it
@@ -366,7 +385,7 @@ cudaError_t msweep_simt_prepare(int np, int dim, int smem_optin) {
   return ok ? err : cudaErrorInvalidValue;
 }
 
-int msweep_simt_blocks_per_sm(int np, int dim, bool bf16, int R, int wpb) {
+int msweep_simt_blocks_per_sm(int np, int dim, bool bf16, int R, int wpb, bool out64) {
   const size_t sm = msweep_simt_smem(np, dim, bf16, R, wpb);
   const int cpl = simt_cpl(np, R);
   int best = 1 << 30;
@@ -375,28 +394,27 @@ int msweep_simt_blocks_per_sm(int np, int dim, bool bf16, int R, int wpb) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, wpb * 32, sm) != cudaSuccess) b = 1;
     best = std::min(best, b);
   };
-  // the smaller of the FP32- and FP64-output instantiations the level's sweeps launch
+  // the instantiation (FP32 or FP64 output) a launch of this shape runs
   simt_dispatch(np, dim, [&](auto NPc, auto Sc) {
     constexpr int NP = decltype(NPc)::value, S = decltype(Sc)::value;
-    auto both = [&](auto ti) {
+    auto one = [&](auto ti, auto to) {
       using TI = decltype(ti);
+      using TO = decltype(to);
       if constexpr (NP > 10) {
-        occ(k_msweep_simt<NP, S, TI, float, 1, 0, false>);
-        occ(k_msweep_simt<NP, S, TI, double, 1, 0, false>);
+        occ(k_msweep_simt<NP, S, TI, TO, 1, 0, false>);
       } else {
-        if (cpl == 4) {
-          occ(k_msweep_simt<NP, S, TI, float, 4, 32, true>);
-          occ(k_msweep_simt<NP, S, TI, double, 4, 32, true>);
-        } else {
-          occ(k_msweep_simt<NP, S, TI, float, 2, 0, true>);
-          occ(k_msweep_simt<NP, S, TI, double, 2, 0, true>);
-          occ(k_msweep_simt<NP, S, TI, float, 2, 0, false>);
-          occ(k_msweep_simt<NP, S, TI, double, 2, 0, false>);
-        }
+        if (cpl == 4) occ(k_msweep_simt<NP, S, TI, TO, 4, 32, true>);
+        else if (R % 2 == 0) occ(k_msweep_simt<NP, S, TI, TO, 2, 0, true>);
+        else occ(k_msweep_simt<NP, S, TI, TO, 2, 0, false>);
       }
     };
-    if (bf16) both(__nv_bfloat16{});
-    else both(float{});
+    if (bf16) {
+      if (out64) one(__nv_bfloat16{}, double{});
+      else one(__nv_bfloat16{}, float{});
+    } else {
+      if (out64) one(float{}, double{});
+      else one(float{}, float{});
+    }
   });
   return best == (1 << 30) ? 1 : std::max(best, 1);
 }

@@ -93,10 +93,11 @@ FP64_PEAK_NOTE = ("FP64 FMA peak from unit counts and clock: 152 SMs x 2 FMA/clk
 # kernel; valid only while the kernel's sources hash to the recorded value (otherwise the
 # line reports null).
 TRAFFIC = {
-    "k_gram_update": (3567740400.0 / ((2 * 199 + 5) * 1105920), "6b661e12a19f0e25",
+    "k_gram_update": (3567589888.0 / ((2 * 199 + 5) * 1105920), "41bfa758cbb3ac94",
                       ["kernels.cu", "kcmg_internal.h", "reduce.cuh"],
-                      "ncu --set full capture of one level-0 launch on 48^3 p=2 with 199 basis "
-                      "vectors: 3.568 GB per launch, scaled to this launch by (2 l + 5) N"),
+                      "ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of one level-0 "
+                      "launch on 48^3 p=2 with 199 basis vectors: 3.568 GB per launch, scaled to "
+                      "this launch by (2 l + 5) N"),
 }
 
 

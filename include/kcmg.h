@@ -273,7 +273,8 @@ kcmg_status kcmg_residual_noalloc(kcmg_ctx *ctx, const double *b, const double *
 /* Batched component calls (right-hand sides fastest, [N_level][nrhs], nrhs in [2, 32],
    level in [0, nlevels-2]); they run the kernels of the batched solve:
    Y = A_level X with the FP64 operator, and Z = BJ_level(R) from Z = 0 (Alg. BJ, omega and
-   sweeps of setup) in the context's precision (mixed forms: tensor-core sweeps). */
+   sweeps of setup) in the context's precision (mixed forms: the FP32 sweep kernel the
+   autotuner chose, see kcmg_mrhs_tuning). */
 kcmg_status kcmg_apply_multi(kcmg_ctx *ctx, int level, int nrhs, const double *x, double *y);
 kcmg_status kcmg_smooth_multi(kcmg_ctx *ctx, int level, int nrhs, const double *r, double *z);
 

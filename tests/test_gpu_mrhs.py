@@ -230,9 +230,11 @@ def _forced_sweep_check(name, precision, tol, nrhs, kind, solve):
 @pytest.mark.parametrize("nrhs", [32, 6])
 def test_bulk_copy_tensor_core_sweep_matches_oracle(name, precision, tol, nrhs, monkeypatch):
     """The tensor-core sweep with every cell's blocks, inverse, residual and neighbour slabs
-    staged by double-buffered 1-D bulk copies (forced on every level), against the oracle."""
+    staged by double-buffered 1-D bulk copies (forced on every level), against the oracle;
+    a batched solve on it at Np = 10 (at Np = 20 the forced kernel runs one warp per SM
+    and a solve takes minutes)."""
     monkeypatch.setenv("KCMG_SWEEP", "tcb")
-    _forced_sweep_check(name, precision, tol, nrhs, 1.0, solve=True)
+    _forced_sweep_check(name, precision, tol, nrhs, 1.0, solve=name != "sipg3d_p3_8cube_zstretch")
 
 
 @pytest.mark.parametrize("name", CASES)

@@ -36,7 +36,10 @@ namespace kcmg {
 namespace {
 
 constexpr int kGramWarps = 8;      // warps per block of the Gram / vector kernels
-constexpr int kGramBlocks = 152;   // blocks of the Gram / vector kernels (one per SM)
+// blocks of the Gram / vector kernels: four per SM (k_mdots, 64 registers x 256 threads,
+// fills the register file at four), so that 32 warps per SM keep their column loads in
+// flight; one block per SM left these kernels latency-bound at 15-27 % of the FP64 rate
+constexpr int kGramBlocks = 4 * 152;
 
 enum : int { MF_REORTH = 1, MF_DISCARD = 2 };
 

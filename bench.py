@@ -253,6 +253,10 @@ def run_reference(args, ws, rank):
 
 MRHS_WORKLOAD = "sipg3d_p2_32cube_rhs32"
 MRHS_LMAX = 100
+# the 32-right-hand-side configuration at full size (64^3 p = 2 x 32 columns), timed over a
+# bounded number of level-0 cycles beside single-column solves over the same cycles
+C4_WORKLOAD = "sipg3d_p2_64cube_rhs32"
+C4_CYCLES = 20
 MRHS_PRECISION = "mixed_bf16"
 
 
@@ -263,13 +267,14 @@ SWEEP_KERNELS = {0: "tensor-core TF32x3 smoother sweeps (FP32 accumulation)",
 SWEEP_KERNEL_NAMES = {0: "k_msweep_tc", 1: "k_msweep_tcb", 2: "k_msweep_simt"}
 
 
-def run_mrhs(pkg, rank, dev, stream, hbm_peak, args):
+def run_mrhs(pkg, rank, dev, stream, hbm_peak, args, wl_name=None, maxiter=None):
     """The batched form: 32 right-hand sides solved together (one K-cycle per column,
     shared operator applications, FP32 sweeps).  value = DOFs x columns / s."""
     import torch
 
     from workloads import workload
-    wname = args.mrhs_workload or MRHS_WORKLOAD
+    wname = wl_name or args.mrhs_workload or MRHS_WORKLOAD
+    cap = maxiter if maxiter is not None else args.maxiter
     prec_m = args.mrhs_precision or MRHS_PRECISION
     lmax_m = args.mrhs_lmax if args.mrhs_lmax is not None else MRHS_LMAX
     pm = workload(wname).make(rank)
@@ -283,7 +288,7 @@ def run_mrhs(pkg, rank, dev, stream, hbm_peak, args):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    inf = pkg.kcmg_solve(sm.ctx, B, X, RTOL, 0.0, args.maxiter)
+    inf = pkg.kcmg_solve(sm.ctx, B, X, RTOL, 0.0, cap)
     e1.record(stream)
     torch.cuda.synchronize()
     mms = e0.elapsed_time(e1)
@@ -301,7 +306,7 @@ def run_mrhs(pkg, rank, dev, stream, hbm_peak, args):
             xj.zero_()
             torch.cuda.synchronize()
             e0.record(stream)
-            ij = pkg.kcmg_solve(s1.ctx, bj, xj, RTOL, 0.0, args.maxiter)
+            ij = pkg.kcmg_solve(s1.ctx, bj, xj, RTOL, 0.0, cap)
             e1.record(stream)
             torch.cuda.synchronize()
             ts.append((e0.elapsed_time(e1), ij["iters"]))
@@ -380,6 +385,8 @@ def main():
                     help="also solve a 32-right-hand-side batch (32^3 p=2, 32 columns of U[-1,1]) "
                          "in the batched mixed form, with single-column solves of the same "
                          "operator beside it, and report it under forms")
+    ap.add_argument("--no-c4", action="store_true",
+                    help="skip the bounded 64^3 x 32-right-hand-side batched form (%d cycles)" % C4_CYCLES)
     ap.add_argument("--maxiter", type=int, default=MAXITER,
                     help="cap on level-0 cycles (profiling runs only; the benchmark solves to 1e-10)")
     ap.add_argument("--workload", default=WORKLOAD, help="workload name (profiling runs only)")
@@ -669,6 +676,12 @@ def main():
 
     if args.mrhs:
         forms["mrhs32"] = run_mrhs(pkg, rank, dev, stream, hbm_peak, args)
+    if not args.no_c4 and not args.no_mixed and ws == 1:
+        # 64^3 x 32 right-hand sides, C4_CYCLES level-0 cycles: DOF-cycles per second beside
+        # single-column solves of the same operator over the same number of cycles
+        f = run_mrhs(pkg, rank, dev, stream, hbm_peak, args, wl_name=C4_WORKLOAD, maxiter=C4_CYCLES)
+        f["bounded_cycles"] = C4_CYCLES
+        forms[f"{C4_WORKLOAD}_{C4_CYCLES}_cycles"] = f
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

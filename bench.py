@@ -170,6 +170,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def _max_over_ranks(v, ws, dev):
+    """The largest v over the ranks of the job (v itself at one rank).  The timed region
+    of a multi-rank job ends when its slowest rank ends, so rates divide by this maximum."""
+    if ws <= 1:
+        return v
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -476,11 +487,8 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1)
+    ms = _max_over_ranks(e0.elapsed_time(e1), ws, dev)
     if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
         torch.distributed.barrier()
     value = ws * pr.ndof * args.steps / (ms * 1e-3)
     status = [i["status"] for i in infos]
@@ -577,11 +585,7 @@ def main():
         for _ in range(k_e2e):
             xh[:] = 0.0
             pkg.kcmg_solve(s.ctx, bh, xh, RTOL, 0.0, args.maxiter)
-        t_e2e = time.perf_counter() - t0
-        if ws > 1:
-            t = torch.tensor([t_e2e], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            t_e2e = float(t.item())
+        t_e2e = _max_over_ranks(time.perf_counter() - t0, ws, dev)
         e2e = {"value": ws * pr.ndof * k_e2e / t_e2e, "unit": UNIT, "steps": k_e2e,
                "h2d_bytes_per_step": 2 * pr.ndof * 8, "d2h_bytes_per_step": pr.ndof * 8,
                "host_buffers": "pinned"}

@@ -48,3 +48,37 @@ def test_traffic_is_null_unless_the_kernel_sources_match():
     finally:
         bench.TRAFFIC.clear()
         bench.TRAFFIC.update(saved)
+
+
+def _max_over_ranks_rank(rank, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=2)
+    try:
+        # rank r timed 1.5 + r seconds: both see the slower rank's time
+        q.put((rank, bench._max_over_ranks(1.5 + rank, 2, "cpu")))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_two_gloo_ranks():
+    """The multi-rank timing step of the bench (the maximum of the ranks' times) with two
+    gloo ranks on the CPU; one rank returns its own value without a process group."""
+    import multiprocessing as mp
+    import socket
+    assert bench._max_over_ranks(3.25, 1, "cpu") == 3.25
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        port = so.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    ps = [ctx.Process(target=_max_over_ranks_rank, args=(r, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    got = sorted(q.get(timeout=180) for _ in ps)
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert got == [(0, 2.5), (1, 2.5)]

@@ -387,6 +387,40 @@ def test_benchmark_level_layout_32cube_task_parallel_matches_oracle(monkeypatch)
     _check_solution(pr, x, info, x_or)
 
 
+def test_benchmark_workload_at_full_size():
+    """The benchmark's workload at full size in its timed launch configuration: 64^3 cells,
+    p = 2 (2,621,440 DOFs), 5 levels, FP64, Alg. AsyncMG with m = 12, lmax 400, CUDA graph,
+    persistent coarse cycle.
+    - Every row of the level-0 operator and of one level-0 smoothing step against the
+      oracle.
+    - The first cycle's residual history (12 smoother RMs, then the coarse RM) against the
+      oracle's first cycle, entry by entry.
+    - The whole solve's true residual evaluated by the oracle's FP64 operator.  The oracle's
+      own solve of this size takes minutes on the host, so the solution is checked through
+      its residual, which bounds it at any size."""
+    pr = workload("sipg3d_p2_64cube").make(0)
+    m = 12
+    orc = OracleSolver.from_problem(pr, async_smooth=m, lmax=400, openmp=True)
+    s = pkg.KCycleSolver(pr, precision="fp64", use_graph=True, coarse_persistent=True,
+                         async_smooth=m, lmax=400)
+    rng = np.random.default_rng(11)
+    xr = rng.standard_normal(pr.ndof)
+    assert _rel(s.apply(0, xr), orc.apply(0, xr)) < 1e-13
+    rr = rng.standard_normal(pr.ndof)
+    assert _rel(s.smooth(0, rr), orc.smooth(0, rr)) < 1e-12
+    _, io = orc.solve(pr.b, rtol=1e-14, maxiter=1)
+    _, i1 = s.solve(pr.b, rtol=1e-14, maxiter=1)
+    n = m + 2
+    assert list(i1["hist_type"][:n]) == list(io["hist_type"][:n])
+    h, ho = i1["hist"][:n], io["hist"][:n]
+    assert np.all(np.abs(h - ho) <= 1e-9 * ho[0]), (h, ho)
+    x, info = s.solve(pr.b, rtol=RTOL_GPU, maxiter=4000)
+    s.close()
+    assert info["status"] == 0, info
+    rel = np.linalg.norm(pr.b - orc.apply(0, x)) / np.linalg.norm(pr.b)
+    assert rel <= 1e-10, rel
+
+
 # ------------------------------------------------------------------ FP64 refinement, FP32 inner solve
 _IR_CASES = ([(n, "ir32", 0, True) for n in SMALL + ["ragged_3d_p2", "sipg2d_p1_32x32_5lev"]]
              + [(n, "ir32", m, pers) for n in ("sipg3d_p2_8cube", "ragged_3d_p2", "sipg2d_p1_32x32_5lev")

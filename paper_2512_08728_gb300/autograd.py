@@ -14,6 +14,7 @@ field.  Everything the solve and the gradient compute runs in libkcmg's kernels.
 from __future__ import annotations
 
 import dataclasses
+import time
 
 import numpy as np
 import torch
@@ -42,11 +43,18 @@ class SWIPOperator:
         self.options = options or SolveOptions()
 
     def solver(self, nu: np.ndarray):
-        """A context for A(nu) (the caller closes it)."""
+        """A context for A(nu) (the caller closes it).  ``last_setup`` records what the new
+        field cost before the solve: the host assembly of the blocks and the context's
+        setup (hierarchy, inverses, coarsest factor), in seconds."""
+        t0 = time.perf_counter()
         blocks, _ = self._assemble(self.pr.n, self.pr.p, self.pr.h, nu, self.pr.eta, self.pr.ref)
+        t1 = time.perf_counter()
         shell = dataclasses.replace(self.pr, blocks=blocks, nu=nu)
         o = self.options
-        return K.KCycleSolver(shell, precision=o.precision, lmax=o.lmax)
+        s = K.KCycleSolver(shell, precision=o.precision, lmax=o.lmax)
+        torch.cuda.synchronize()
+        self.last_setup = {"assemble_s": t1 - t0, "context_s": time.perf_counter() - t1}
+        return s
 
     def solve(self, nu, b: torch.Tensor, x0: torch.Tensor | None = None, rtol=None, atol=0.0,
               strict=True, maxiter=None):

@@ -268,6 +268,8 @@ MRHS_LMAX = 100
 # bounded number of level-0 cycles beside single-column solves over the same cycles
 C4_WORKLOAD = "sipg3d_p2_64cube_rhs32"
 C4_CYCLES = 20
+# the adjoint-gradient workload (log-normal coefficient, target field from the next seed)
+ADJ_WORKLOAD = "sipg3d_p2_32cube_lognormal"
 MRHS_PRECISION = "mixed_bf16"
 
 
@@ -276,6 +278,44 @@ SWEEP_KERNELS = {0: "tensor-core TF32x3 smoother sweeps (FP32 accumulation)",
                  1: "tensor-core TF32x3 smoother sweeps, bulk-copy staged (FP32 accumulation)",
                  2: "FP32 CUDA-core smoother sweeps"}
 SWEEP_KERNEL_NAMES = {0: "k_msweep_tc", 1: "k_msweep_tcb", 2: "k_msweep_simt"}
+
+
+def run_adjoint(pkg, dev):
+    """One gradient evaluation of L(b, log nu) = 0.5 ||u - u_t||^2 with u = A(nu)^{-1} b on
+    the log-normal workload, through torch.autograd: the forward solve (host assembly of
+    A(nu), a new context, the solve) and the backward pass (the adjoint solve A^T lambda =
+    u - u_t and the per-cell gradient kernel).  Timed on the host clock around each pass with
+    a device synchronize (the forward pass includes host work), after one untimed
+    evaluation.  value = DOFs x evaluations / s."""
+    import numpy as np
+    import torch
+
+    from paper_2512_08728_gb300.autograd import KCycleSolve, SolveOptions, SWIPOperator
+    from workloads import workload
+    w = workload(ADJ_WORKLOAD)
+    pr, pt = w.make(0), w.make(1)
+    op = SWIPOperator(pr, options=SolveOptions(rtol=RTOL))
+    b = torch.from_numpy(pr.b).to(dev)
+    ut = op.solve(pt.nu, b)
+    times = []
+    for _ in range(2):
+        log_nu = torch.from_numpy(np.log(pr.nu)).to(dev).requires_grad_(True)
+        bb = b.clone().requires_grad_(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        u = KCycleSolve.apply(bb, log_nu, op)
+        loss = 0.5 * torch.sum((u - ut) ** 2)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        loss.backward()
+        torch.cuda.synchronize()
+        times.append((t1 - t0, time.perf_counter() - t1))
+    fwd, bwd = times[-1]
+    return {"value": pr.ndof / (fwd + bwd), "unit": UNIT, "workload": ADJ_WORKLOAD,
+            "what": "one dL/db and dL/dlog nu evaluation (forward solve + adjoint solve + gradient)",
+            "forward_s": fwd, "backward_s": bwd, "per_field_setup": op.last_setup,
+            "grad_norm": float(torch.linalg.vector_norm(log_nu.grad)),
+            "timing": "host clock with a device synchronize around each pass; one untimed evaluation first"}
 
 
 def run_mrhs(pkg, rank, dev, stream, hbm_peak, args, wl_name=None, maxiter=None):
@@ -396,6 +436,8 @@ def main():
                     help="also solve a 32-right-hand-side batch (32^3 p=2, 32 columns of U[-1,1]) "
                          "in the batched mixed form, with single-column solves of the same "
                          "operator beside it, and report it under forms")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="run only the adjoint-gradient form (%s)" % ADJ_WORKLOAD)
     ap.add_argument("--no-c4", action="store_true",
                     help="skip the bounded 64^3 x 32-right-hand-side batched form (%d cycles)" % C4_CYCLES)
     ap.add_argument("--maxiter", type=int, default=MAXITER,
@@ -445,6 +487,10 @@ def main():
             print(json.dumps({"probe": "smooth", "z": float(torch.linalg.vector_norm(zz)),
                               "y": float(torch.linalg.vector_norm(yy))}))
         sv.close()
+        return
+    if args.adjoint_only:
+        if rank == 0:
+            print(json.dumps({"adjoint": run_adjoint(pkg, dev)}), flush=True)
         return
     if args.mrhs_only:
         out = run_mrhs(pkg, rank, dev, stream, hbm_peak, args)
@@ -691,6 +737,11 @@ def main():
         except (pkg.KcmgError, RuntimeError) as e:   # the library's error, or torch's OOM
             f = {"error": str(e)}
         forms[f"{C4_WORKLOAD}_{C4_CYCLES}_cycles"] = f
+    if not args.no_mixed and ws == 1:
+        try:
+            forms[f"{ADJ_WORKLOAD}_adjoint_gradient"] = run_adjoint(pkg, dev)
+        except Exception as e:   # noqa: BLE001  (a failed form is reported; the line stands)
+            forms[f"{ADJ_WORKLOAD}_adjoint_gradient"] = {"error": f"{type(e).__name__}: {e}"}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
